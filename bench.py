@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of C = A B over GF(2) on GB300: square n = 32768, Bernoulli(1/2) bits.
+
+One step is one whole product through the library: Strassen-Winograd
+additions (Algorithm 4) at every level, the base case on all leaves, and the
+recombination.  The packed Method-of-the-Four-Russians base case and the
+tensor-core base case are timed side by side on the same resident inputs;
+the faster one is the headline.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank multiplies its own pair of matrices (the
+problems are independent, no data-path collective); the value is the bit
+operations of all ranks over the slowest rank's time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "effective GF(2) bit-ops/s (2mnk/t) at n=32768, bit-exact"
+UNIT = "bit-ops/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--paths", default="m4rm,tc_fp8", help="base cases to time")
+    ap.add_argument("--depth", type=int, default=-1)
+    ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--t", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target duration of one CPU-oracle sample")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
+    """Roofline of the dominant kernel from its algorithmic work per launch."""
+    if ms_per_launch <= 0:
+        return None
+    if fam == "tc_fp8":
+        flops = 2.0 * M * L * N * leaves                    # dense 0/1 product, exact sums
+        achieved = flops / (ms_per_launch * 1e-3) / 1e12
+        peak = 2.0 * peaks["bf16_tflops"]                    # FP8 = 2 x BF16 (nominal ratio)
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_note": "2 x bf16 burst of %s peaks (nominal fp8/bf16 ratio)" % peak_kind}
+    # packed M4RM: table-row reads from shared memory, M*L*N/(8k) bytes per product
+    smem_bytes = M * L * N / (8.0 * k) * leaves
+    achieved = smem_bytes / (ms_per_launch * 1e-3) / 1e9
+    peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+    return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_note": "152 SMs x 128 B/clk x %.0f MHz (shared-memory bandwidth)" %
+                         peaks.get("sm_max_mhz", 2070.0)}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_0811_1714_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    g.lib()
+    n = l = m = args.n
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+
+    A = g.empty(m, l)
+    B = g.empty(l, n)
+    C = g.empty(m, n)
+    MA, MB, MC = g.mat(A, l), g.mat(B, n), g.mat(C, n)
+    g.gf2_random(MA, 1 + 100 * rank)
+    g.gf2_random(MB, 2 + 100 * rank)
+    torch.cuda.synchronize()
+    peaks, peak_kind = load_peaks()
+
+    avail = [p.strip() for p in args.paths.split(",") if p.strip()]
+    base_of = {"m4rm": g.GF2_BASE_M4RM, "tc_fp8": g.GF2_BASE_TC_FP8}
+    results = {}
+    for path in avail:
+        o = g.opts(base=base_of[path], depth=args.depth, k=args.k if path == "m4rm" else 0,
+                   t=args.t if path == "m4rm" else 0)
+        try:
+            plan = g.gf2_describe_plan(m, l, n, o)
+            g.gf2_mul(MC, MA, MB, o)
+        except g.GF2Error as e:
+            results[path] = {"unavailable": str(e)}
+            continue
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            g.gf2_mul(MC, MA, MB, o)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        launches0 = g.gf2_launch_count()
+        g.gf2_profile_enable(True)
+        with ClockSampler(local_rank) as cs:
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                g.gf2_mul(MC, MA, MB, o)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms_total = ev0.elapsed_time(ev1)
+        launches = g.gf2_launch_count() - launches0
+        fam = {}
+        for i, name in enumerate(g.PROFILE_FAMILIES):
+            t, c = g.gf2_profile_read(i)
+            if c:
+                fam[name] = {"ms": t, "launches": c}
+        g.gf2_profile_enable(False)
+        if dist is not None:
+            tt = torch.tensor([ms_total], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms_total = float(tt.item())
+        ms = ms_total / args.steps
+        bad = g.gf2_freivalds(MC, MA, MB, 1000 + rank)
+        # plan fields
+        kv = dict(x.split("=", 1) for x in plan.split() if "=" in x)
+        d = int(kv["depth"])
+        M, L, N = (int(x) for x in kv["leaf"].split("x"))
+        leaves = int(kv["leaves"])
+        k = int(kv.get("m4rm_k", 8))
+        dom = max(fam.items(), key=lambda kvp: kvp[1]["ms"])[0] if fam else path
+        dom_ms = fam[dom]["ms"] / max(fam[dom]["launches"], 1) if fam else 0.0
+        rl = roofline_for(dom, leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
+            if dom in ("m4rm", "tc_fp8") else None
+        results[path] = {
+            "ms": ms, "value": 2.0 * m * l * n * world / (ms * 1e-3), "depth": d, "plan": plan,
+            "gpu_launches": launches, "kernels": fam, "dominant": dom,
+            "dominant_ms_per_launch": dom_ms, "roofline": rl,
+            "freivalds_mismatched_rows": bad, "clocks": cs.summary(),
+        }
+    ok = {p: r for p, r in results.items() if "ms" in r}
+    if not ok:
+        raise SystemExit("no base case ran: %s" % results)
+    head = min(ok, key=lambda p: ok[p]["ms"])
+    H = ok[head]
+
+    e2e = None
+    if not args.no_e2e:
+        # the same product through the public C ABI on pinned HOST buffers:
+        # H2D of A and B, the product, D2H of C, every step
+        hA = A.cpu().pin_memory()
+        hB = B.cpu().pin_memory()
+        hC = torch.zeros_like(C, device="cpu").pin_memory()
+        o = g.opts(base=base_of[head], depth=args.depth)
+        hMA, hMB, hMC = g.mat(hA, l), g.mat(hB, n), g.mat(hC, n)
+        for _ in range(max(1, args.warmup)):
+            g.gf2_mul(hMC, hMA, hMB, o)
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g.gf2_mul(hMC, hMA, hMB, o)         # returns after the D2H copy completed
+        t_e2e = (time.perf_counter() - t0) / args.steps
+        if dist is not None:
+            tt = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        same = bool(torch.equal(hC.cuda(), C))
+        e2e = {"value": 2.0 * m * l * n * world / t_e2e, "unit": UNIT,
+               "ms_per_step": t_e2e * 1e3,
+               "h2d_bytes_per_step": (hA.numel() + hB.numel()) * 8,
+               "d2h_bytes_per_step": hC.numel() * 8, "matches_device_result": same}
+
+    line = {
+        "metric": METRIC, "value": H["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64-packed-bits" if head == "m4rm" else "fp8e4m3-0/1",
+        "data": "synthetic: SplitMix64 Bernoulli(1/2) bits, seeds 1/2 (+100*rank)",
+        "config": {"workload": "square C=A*B over GF(2), m=l=n=%d" % n, "m": m, "l": l, "n": n,
+                   "base": head, "depth": H["depth"], "plan": H["plan"],
+                   "parallelism": "independent product per GPU" if world > 1 else "single GPU",
+                   "l2": "inputs 2 x %d MiB + output %d MiB exceed the 129 MB L2" % (
+                       m * l // 8 // 2**20, m * n // 8 // 2**20)},
+        "roofline": H["roofline"], "gpu_launches": H["gpu_launches"],
+        "clocks": H["clocks"], "e2e": e2e,
+        "verified": {"freivalds_64_vectors_mismatched_rows": H["freivalds_mismatched_rows"]},
+        "paths": {p: {kk: vv for kk, vv in r.items() if kk not in ("plan",)} for p, r in results.items()},
+        "cpu_baseline": None,
+    }
+    return line
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sample(n, target_s, seed_a=1, seed_b=2):
+    """Time the CPU oracle on rows 0..r-1 of C for the n x n workload; r is
+    chosen so that one sample takes about target_s seconds."""
+    import oracle
+    import synth
+    B = synth.random_packed(n, n, seed_b)
+    r = 2
+    while True:
+        A = synth.random_packed(r, n, seed_a)
+        t0 = time.perf_counter()
+        oracle.mul_packed(A, B, r, n, n)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or r >= n:
+            return r, dt
+        r = min(n, max(r * 2, int(r * target_s / max(dt, 1e-3) * 0.9)))
+
+
+def cpu_baseline(n, target_s):
+    import oracle
+    r, dt = oracle_sample(n, target_s)
+    return {"value": 2.0 * r * n * n / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": "rows 0..%d of C = A B at n=%d (naive cubic on unpacked bytes, "
+                      "unpacking included), %.1f s" % (r - 1, n, dt)}
+
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores: each step one bounded sample."""
+    import oracle
+    import synth
+    n = args.n
+    r, _ = oracle_sample(n, max(1.0, min(args.cpu_seconds, 20.0)))
+    B = synth.random_packed(n, n, 2)
+    A = synth.random_packed(r, n, 1)
+    for _ in range(args.warmup):
+        oracle.mul_packed(A, B, r, n, n)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.mul_packed(A, B, r, n, n)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = 2.0 * r * n * n / dt
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8-unpacked",
+        "data": "synthetic: SplitMix64 Bernoulli(1/2) bits, seeds 1/2",
+        "config": {"workload": "square C=A*B over GF(2), m=l=n=%d" % n, "m": n, "l": n, "n": n,
+                   "sample_rows": r},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "rows 0..%d of C per step (naive cubic oracle)" % (r - 1)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * gf2.h -- C ABI of libgf2: dense matrix multiplication over GF(2) on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Albrecht, Bard and Hart, "Efficient Multiplication of Dense
+ * Matrices over GF(2)".  C = A B where addition is XOR and multiplication is
+ * AND (Abstract).  The product runs Strassen-Winograd recursion (Section 4,
+ * Algorithm 4) down to a base case, which is either the Method of the Four
+ * Russians (Section 3, Algorithms 1-3) on bit-packed words, or an exact
+ * tensor-core form that multiplies 0/1 values and keeps the parity of each
+ * integer dot product (Section 2.3: a GF(2) dot product is an AND followed by
+ * an XOR accumulation, i.e. the integer dot product mod 2).
+ *
+ * Matrix layout (Section 2.1, "flat row-major representation"): 64
+ * consecutive entries of a row are packed into one 64-bit word.  Entry
+ * (r, c) is bit (c % 64) of word data[r * stride_words + c / 64].
+ * stride_words >= ceil(cols / 64); the library requires it to be even and
+ * `data` to be 16-byte aligned (rows are read with 128-bit loads).
+ * Bits of columns >= cols are IGNORED on input and written as 0 on output.
+ *
+ * Conventions for every call:
+ *  - return GF2_OK (0) on success, a negative GF2_E* status otherwise;
+ *    nothing is launched when a call fails its argument checks;
+ *  - device work is asynchronous on `cuda_stream` (a cudaStream_t; NULL is
+ *    the legacy default stream).  Results are valid once the stream has
+ *    reached the point after the call;
+ *  - the caller owns every gf2_mat; the library owns only its scratch arenas
+ *    (one per device and stream, grown on demand, released by
+ *    gf2_release_scratch) and its autotuning cache;
+ *  - a matrix with device >= 0 lives in that device's global memory; with
+ *    device == GF2_HOST it lives in host memory (pinned memory gives full
+ *    copy speed).  gf2_mul accepts host operands and then copies them
+ *    through its device scratch inside the call.
+ */
+#ifndef GF2_H
+#define GF2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define GF2_OK            0
+#define GF2_EINVAL       (-1)  /* NULL pointer, negative size, A.cols != B.rows, C not m x n, bad option */
+#define GF2_EALIAS       (-2)  /* C overlaps A or B                                           */
+#define GF2_ELAYOUT      (-3)  /* stride < ceil(cols/64), odd stride, or data not 16-byte aligned */
+#define GF2_ENOMEM       (-4)  /* device or host allocation failed                            */
+#define GF2_ECUDA        (-5)  /* CUDA runtime / launch error                                 */
+#define GF2_ETIMEOUT     (-6)  /* a bounded device-side wait expired                          */
+#define GF2_EUNSUPPORTED (-7)  /* option not available for this shape or device               */
+#define GF2_EMISMATCH    (-8)  /* verification found C != A B                                 */
+
+#define GF2_HOST (-1)          /* gf2_mat.device value for host memory */
+
+/* ---- base cases -------------------------------------------------------- */
+#define GF2_BASE_AUTO   0      /* autotuner's choice                                         */
+#define GF2_BASE_M4RM   1      /* Method of the Four Russians on packed words (Sections 3.x) */
+#define GF2_BASE_TC_FP8 2      /* 0/1 FP8 e4m3 tensor-core product, parity of exact sums    */
+
+typedef struct gf2_mat {
+    uint64_t *data;        /* first word of row 0                                  */
+    int64_t rows;          /* number of rows                                       */
+    int64_t cols;          /* number of entries per row                            */
+    int64_t stride_words;  /* words between the starts of consecutive rows         */
+    int32_t device;        /* CUDA device ordinal, or GF2_HOST                     */
+    int32_t reserved;
+} gf2_mat;
+
+typedef struct gf2_opts {
+    int32_t base;          /* GF2_BASE_*                                                 */
+    int32_t depth;         /* Strassen-Winograd levels: -1 = auto, 0 = base case only    */
+    int32_t k;             /* M4RM bits per table (Section 3.1 "k"): 0 = auto, else 4..10 */
+    int32_t t;             /* M4RM tables per pass (Section 3.3 "t"): 0 = auto            */
+    int32_t accumulate;    /* 0: C = A B;  1: C ^= A B                                    */
+    int32_t reserved[3];   /* must be 0                                                   */
+} gf2_opts;
+
+/* Fill *opts with the defaults (everything automatic, C = A B). */
+void gf2_default_opts(gf2_opts *opts);
+
+/* Message for a status code (static string, never NULL). */
+const char *gf2_strerror(int status);
+
+/* ---- memory -------------------------------------------------------------
+ * gf2_alloc: device matrix on the CURRENT CUDA device, zero-filled, stride
+ * ceil(cols/64) rounded up to even.  rows or cols may be 0 (data is then
+ * NULL).  On failure *M is left with data == NULL.
+ * gf2_free: releases what gf2_alloc returned; idempotent (data set to NULL).
+ * Both synchronise with the device (cudaMalloc / cudaFree semantics).
+ */
+int gf2_alloc(gf2_mat *M, int64_t rows, int64_t cols);
+int gf2_free(gf2_mat *M);
+
+/* ---- the product ---------------------------------------------------------
+ * C = A B  (or C ^= A B with opts->accumulate), A m x l, B l x n, C m x n.
+ * Section 4 (Algorithm 4) recursion to opts->depth levels -- operands are
+ * zero-padded virtually to even, word-aligned sizes (Section 4, "padding")
+ * -- then the base case of opts->base on all 7^depth leaf products at once.
+ * Temporaries live in the scratch arena of (device, stream).  opts may be
+ * NULL (defaults).  C must not overlap A or B (GF2_EALIAS).  Zero-sized
+ * operands are valid: C is cleared (or left alone when accumulating).
+ * Device operands must all be on the current device; host operands
+ * (device == GF2_HOST) are copied in and C is copied back inside the call,
+ * which then returns only after the stream has finished it.
+ */
+int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B,
+            const gf2_opts *opts, void *cuda_stream);
+
+/* ---- batched products ----------------------------------------------------
+ * C[i] = A[i] B[i] for i < count, independent shapes, one launch of a
+ * persistent kernel that pulls tiles of all products from one work queue
+ * (device operands only).  Same per-product rules as gf2_mul.
+ */
+int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[],
+                    const gf2_mat *const B[], int32_t count,
+                    const gf2_opts *opts, void *cuda_stream);
+
+/* ---- steps of the path, callable alone ------------------------------------
+ * gf2_sw_split: the 8 additions of Algorithm 4 for one level.  From X
+ * (rows x cols, both even, cols a multiple of 128) writes the 7 operands of
+ * the products P0..P6 into out[0..6] (each rows/2 x cols/2, dense stride
+ * cols/128 words rounded up to even, out[i] = base + i * slab_words).
+ * side = 0 treats X as the left factor A: out = A_NW, A_NE, S3, A_SE, S0, S1,
+ * S2 with S0 = A_SW+A_SE, S1 = S0+A_NW, S2 = A_NW+A_SW, S3 = A_NE+S1.
+ * side = 1 treats X as the right factor B: out = B_NW, B_SW, B_SE, T3, T0, T1,
+ * T2 with T0 = B_NE+B_NW, T1 = B_SE+T0, T2 = B_SE+B_NE, T3 = T1+B_SW.
+ * (Over GF(2) every "-" of Algorithm 4 is "+" = XOR.)
+ */
+int gf2_sw_split(uint64_t *out, int64_t slab_words, const gf2_mat *X,
+                 int32_t side, void *cuda_stream);
+
+/* gf2_sw_combine: the 7 final additions of Algorithm 4 plus Augment/Stack.
+ * P holds the 7 products P0..P6 (each rows/2 x cols/2, dense layout as
+ * written by gf2_sw_split, P[i] = base + i * slab_words); writes
+ * C = [[U0, U4], [U5, U6]] into the rows x cols matrix C.
+ */
+int gf2_sw_combine(gf2_mat *C, const uint64_t *P, int64_t slab_words,
+                   void *cuda_stream);
+
+/* gf2_make_table: the table of Algorithm 1's MakeTable for one stripe:
+ * T[x] = sum of rows r0+j of B (all columns) over the bits j set in x, for
+ * x < 2^k (bit j of x selects row r0+j; rows >= B.rows count as zero).
+ * T is a 2^k x B.cols device matrix.  1 <= k <= 10.
+ */
+int gf2_make_table(gf2_mat *T, const gf2_mat *B, int64_t r0, int32_t k,
+                   void *cuda_stream);
+
+/* ---- helpers ---------------------------------------------------------------
+ * gf2_random: fill a device matrix with the seeded SplitMix64 bits (p = 0.5
+ * takes whole outputs; otherwise one 32-bit uniform per bit), tail bits and
+ * padding words 0.  Word (r, w) uses output r*ceil(cols/64)+w+1 of the stream
+ * seeded with `seed` (p = 0.5), or outputs (r*W+w)*32+j+1, j < 32 (p != 0.5).
+ */
+int gf2_random(gf2_mat *M, uint64_t seed, double p, void *cuda_stream);
+
+/* gf2_transpose: T = X^T (T is X.cols x X.rows). */
+int gf2_transpose(gf2_mat *T, const gf2_mat *X, void *cuda_stream);
+
+/* gf2_freivalds: checks C == A B with 64 random vectors at once (Freivalds'
+ * test): X = seeded n x 64 bits, compares A (B X) with C X.  A wrong C
+ * passes with probability <= 2^-64.  *mismatched_rows receives the number of
+ * rows of A(BX) + CX that are non-zero (0 means the check passed).  Blocks
+ * the calling thread until the stream has finished the check.
+ */
+int gf2_freivalds(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B,
+                  uint64_t seed, int64_t *mismatched_rows, void *cuda_stream);
+
+/* ---- scratch ---------------------------------------------------------------
+ * gf2_scratch_bytes: device scratch that gf2_mul needs for these shapes and
+ * options (0 when it needs none).
+ * gf2_reserve_scratch: grow the arena of (current device, stream) to at
+ * least `bytes` now, so that later calls do not allocate.
+ * gf2_release_scratch: free every arena of the current device (synchronises
+ * the device first).
+ */
+int64_t gf2_scratch_bytes(int64_t m, int64_t l, int64_t n, const gf2_opts *opts);
+int gf2_reserve_scratch(int64_t bytes, void *cuda_stream);
+int gf2_release_scratch(void);
+
+/* Number of kernels this library has launched in this process (all devices). */
+int64_t gf2_launch_count(void);
+
+/* ---- device-time accounting ----------------------------------------------
+ * gf2_profile_enable(1) clears the counters and starts bracketing every
+ * kernel launch of the library with CUDA events on its stream; (0) stops.
+ * gf2_profile_read waits for the recorded events and returns the summed
+ * device time (ms) and launch count of one kernel family:
+ *   0 m4rm base case, 1 tensor-core base case, 2 Strassen split,
+ *   3 Strassen combine, 4 transpose, 5 generator, 6 Freivalds products,
+ *   7 MakeTable, 8 batched base case.
+ * gf2_profile_name gives the family's name (NULL beyond the last one).
+ */
+int gf2_profile_enable(int32_t on);
+int gf2_profile_read(int32_t family, double *ms, int64_t *launches);
+const char *gf2_profile_name(int32_t family);
+
+/* Plan that gf2_mul would use for these shapes and options, as text (for
+ * logs and tests): writes at most `cap` bytes including the terminating NUL.
+ */
+int gf2_describe_plan(int64_t m, int64_t l, int64_t n, const gf2_opts *opts,
+                      char *buf, int32_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GF2_H */

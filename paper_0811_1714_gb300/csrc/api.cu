@@ -1,0 +1,691 @@
+// api.cu -- the C ABI of libgf2: argument checks, the Strassen-Winograd
+// plan (Section 4, Algorithm 4) with its scratch arena, dispatch to the base
+// cases, host staging, and Freivalds' check.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+namespace gf2 {
+long long launch_count();
+int profile_enable(int on);
+int profile_read(int fam, double *ms, long long *n);
+}
+
+using namespace gf2;
+
+namespace {
+
+// ---------------------------------------------------------------- arenas
+struct Arena {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_arena_mu;
+std::map<std::pair<int, uintptr_t>, Arena> g_arenas;
+
+int arena_get(cudaStream_t s, size_t bytes, void **out)
+{
+    *out = nullptr;
+    if (bytes == 0) return GF2_OK;
+    int dev = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    Arena &a = g_arenas[{dev, reinterpret_cast<uintptr_t>(s)}];
+    if (a.bytes < bytes) {
+        if (a.ptr) {
+            // earlier work queued on this stream may still use the old arena
+            GF2_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(a.ptr);
+            a.ptr = nullptr;
+            a.bytes = 0;
+        }
+        const size_t want = (bytes + (1u << 21) - 1) & ~(size_t)((1u << 21) - 1);
+        if (cudaMalloc(&a.ptr, want) != cudaSuccess) {
+            cudaGetLastError();
+            a.ptr = nullptr;
+            return GF2_ENOMEM;
+        }
+        a.bytes = want;
+    }
+    *out = a.ptr;
+    return GF2_OK;
+}
+
+// ---------------------------------------------------------------- checks
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int check_mat(const gf2_mat *M)
+{
+    if (!M) return GF2_EINVAL;
+    if (M->rows < 0 || M->cols < 0) return GF2_EINVAL;
+    if (M->rows == 0 || M->cols == 0) return GF2_OK;
+    if (!M->data) return GF2_EINVAL;
+    if (M->stride_words < words_of(M->cols)) return GF2_ELAYOUT;
+    if ((M->stride_words & 1) || !aligned16(M->data)) return GF2_ELAYOUT;
+    return GF2_OK;
+}
+
+size_t mat_bytes(const gf2_mat *M)
+{
+    if (M->rows == 0 || M->cols == 0) return 0;
+    return (size_t)((M->rows - 1) * M->stride_words + words_of(M->cols)) * 8;
+}
+
+bool overlaps(const gf2_mat *X, const gf2_mat *Y)
+{
+    if (X->device != Y->device) return false;
+    const size_t bx = mat_bytes(X), by = mat_bytes(Y);
+    if (!bx || !by) return false;
+    const uintptr_t x0 = reinterpret_cast<uintptr_t>(X->data), y0 = reinterpret_cast<uintptr_t>(Y->data);
+    return x0 < y0 + by && y0 < x0 + bx;
+}
+
+gf2_opts resolve(const gf2_opts *o)
+{
+    gf2_opts r;
+    gf2_default_opts(&r);
+    if (o) r = *o;
+    return r;
+}
+
+int check_opts(const gf2_opts &o)
+{
+    if (o.base < GF2_BASE_AUTO || o.base > GF2_BASE_TC_FP8) return GF2_EINVAL;
+    if (o.depth < -1 || o.depth > 8) return GF2_EINVAL;
+    if (o.k < 0 || o.k > 10 || o.t < 0 || o.t > 16) return GF2_EINVAL;
+    if (o.accumulate != 0 && o.accumulate != 1) return GF2_EINVAL;
+    if (o.reserved[0] || o.reserved[1] || o.reserved[2]) return GF2_EINVAL;
+    if (o.k > 0 && o.t > 0 && !m4rm_supported(o.k, o.t)) return GF2_EUNSUPPORTED;
+    return GF2_OK;
+}
+
+// ---------------------------------------------------------------- the plan
+// Strassen-Winograd, breadth first (Algorithm 4 applied `depth` times to all
+// sub-problems of a level at once).  Padded sizes: rows to a multiple of
+// 2^depth, column counts to a multiple of 128 * 2^depth so that every
+// quadrant starts on a 16-byte boundary (Section 4's "good" sizes, reached
+// by virtual zero padding).  Arena: A-operand, B-operand and product slabs of
+// every level, then the transposed B for the tensor-core base, then host
+// staging buffers.
+constexpr int kMaxDepth = 8;
+
+struct Plan {
+    int64_t m, l, n;
+    int base;
+    int depth;
+    int64_t M, L, N;
+    int k, t;
+    // per level j (1..depth): offsets (bytes) and strides (words)
+    size_t offA[kMaxDepth + 1], offB[kMaxDepth + 1], offP[kMaxDepth + 1];
+    int64_t ldA[kMaxDepth + 1], ldB[kMaxDepth + 1], ldP[kMaxDepth + 1];
+    int64_t slabA[kMaxDepth + 1], slabB[kMaxDepth + 1], slabP[kMaxDepth + 1];
+    size_t offBt;        // transposed B (tensor-core base, depth 0 or top of the split)
+    int64_t ldBt;
+    size_t bytes;        // total device scratch (without host staging)
+};
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+int auto_depth(int64_t m, int64_t l, int64_t n, int base)
+{
+    // Recurse while every dimension of the sub-problems stays at or above the
+    // cutoff (Section 5's c_o): each level saves 1/8 of the base-case work
+    // and costs O(n^2) streaming additions.
+    const int64_t cutoff = (base == GF2_BASE_TC_FP8) ? 8192 : 4096;
+    int d = 0;
+    int64_t mm = m, ll = l, nn = n;
+    while (d < 6 && mm / 2 >= cutoff && ll / 2 >= cutoff && nn / 2 >= cutoff) {
+        mm /= 2; ll /= 2; nn /= 2; ++d;
+    }
+    return d;
+}
+
+int make_plan(int64_t m, int64_t l, int64_t n, const gf2_opts &o, Plan *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->m = m; p->l = l; p->n = n;
+    p->base = o.base;
+    if (p->base == GF2_BASE_AUTO) p->base = GF2_BASE_M4RM;
+    if (p->base == GF2_BASE_TC_FP8 && !tc_fp8_available()) return GF2_EUNSUPPORTED;
+    p->depth = (o.depth < 0) ? auto_depth(m, l, n, p->base) : o.depth;
+    if (m == 0 || n == 0 || l == 0) p->depth = 0;
+    const int d = p->depth;
+    const int64_t rq = (int64_t)1 << d, cq = (int64_t)128 << d;
+    p->M = d ? round_up(m, rq) : m;
+    p->L = d ? round_up(l, cq) : l;
+    p->N = d ? round_up(n, cq) : n;
+    if (d && (p->M < 2 * rq / 2 || p->M / rq < 1)) return GF2_EUNSUPPORTED;
+    p->k = o.k; p->t = o.t;
+    const bool tc = (p->base == GF2_BASE_TC_FP8);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off += (bytes + 255) & ~(size_t)255;
+        return at;
+    };
+    int64_t cnt = 1;
+    for (int j = 1; j <= d; ++j) {
+        cnt *= 7;
+        const int64_t Mj = p->M >> j, Lj = p->L >> j, Nj = p->N >> j;
+        p->ldA[j] = Lj / 64;
+        p->slabA[j] = Mj * p->ldA[j];
+        p->offA[j] = take((size_t)(cnt * p->slabA[j]) * 8);
+        if (tc) {   // right factors stored transposed: Nj x Lj
+            p->ldB[j] = Lj / 64;
+            p->slabB[j] = Nj * p->ldB[j];
+        } else {
+            p->ldB[j] = Nj / 64;
+            p->slabB[j] = Lj * p->ldB[j];
+        }
+        p->offB[j] = take((size_t)(cnt * p->slabB[j]) * 8);
+        p->ldP[j] = Nj / 64;
+        p->slabP[j] = Mj * p->ldP[j];
+        p->offP[j] = take((size_t)(cnt * p->slabP[j]) * 8);
+    }
+    if (tc) {
+        p->ldBt = even_up(words_of(l));
+        p->offBt = take((size_t)(n * p->ldBt) * 8);
+    }
+    p->bytes = off;
+    return GF2_OK;
+}
+
+std::string plan_text(const Plan &p)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf,
+             "base=%s depth=%d padded=%lldx%lldx%lld leaves=%lld leaf=%lldx%lldx%lld k=%d t=%d scratch=%zu",
+             p.base == GF2_BASE_TC_FP8 ? "tc_fp8" : "m4rm", p.depth, (long long)p.M, (long long)p.L,
+             (long long)p.N, (long long)[&] { long long c = 1; for (int j = 0; j < p.depth; ++j) c *= 7; return c; }(),
+             (long long)(p.M >> p.depth), (long long)(p.L >> p.depth), (long long)(p.N >> p.depth), p.k, p.t,
+             p.bytes);
+    return buf;
+}
+
+// Base case over `batch` products with dense or user layouts.
+int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const uint64_t *B,
+             int64_t ldb, int64_t bsB, uint64_t *C, int64_t ldc, int64_t bsC, int64_t m, int64_t l,
+             int64_t n, int batch, int accumulate, cudaStream_t s)
+{
+    if (p.base == GF2_BASE_TC_FP8) {
+        TcLaunch L;
+        L.A = A; L.lda = lda; L.bsA = bsA;
+        L.Bt = B; L.ldb = ldb; L.bsB = bsB;
+        L.C = C; L.ldc = ldc; L.bsC = bsC;
+        L.m = m; L.l = l; L.n = n; L.batch = batch; L.accumulate = accumulate;
+        L.status = nullptr;
+        return tc_fp8_launch(L, s);
+    }
+    M4rmLaunch L;
+    L.A = A; L.lda = lda; L.bsA = bsA;
+    L.B = B; L.ldb = ldb; L.bsB = bsB;
+    L.C = C; L.ldc = ldc; L.bsC = bsC;
+    L.m = m; L.l = l; L.n = n; L.batch = batch; L.accumulate = accumulate;
+    L.k = p.k; L.t = p.t; L.ksplit = 0; L.bm = 0;
+    return m4rm_launch(L, s);
+}
+
+// C = A B (or C ^= A B) for device matrices on the current device.
+int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan &p, int accumulate,
+               char *scratch, cudaStream_t s)
+{
+    const int64_t m = p.m, l = p.l, n = p.n;
+    if (m == 0 || n == 0) return GF2_OK;
+    if (l == 0) {
+        if (accumulate) return GF2_OK;
+        GF2_CUDA_TRY(cudaMemset2DAsync(C->data, C->stride_words * 8, 0, words_of(n) * 8, m, s));
+        return GF2_OK;
+    }
+    const bool tc = (p.base == GF2_BASE_TC_FP8);
+    const uint64_t *Bsrc = B->data;
+    int64_t ldBsrc = B->stride_words;
+    if (tc) {
+        uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
+        DMat T{Bt, n, l, p.ldBt};
+        DMat X{B->data, l, n, B->stride_words};
+        int rc = transpose_launch(T, X, s);
+        if (rc) return rc;
+        Bsrc = Bt;
+        ldBsrc = p.ldBt;
+    }
+    const int d = p.depth;
+    if (d == 0)
+        return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
+                        m, l, n, 1, accumulate, s);
+
+    // top-down: the 8 additions of Algorithm 4 for every sub-problem of each level
+    int64_t cnt = 1;
+    for (int j = 1; j <= d; ++j) {
+        const int64_t Mp = p.M >> (j - 1), Lp = p.L >> (j - 1), Np = p.N >> (j - 1);
+        SplitLaunch SA;
+        SA.nparent = (int)cnt;
+        SA.side = 0;
+        SA.rows = Mp; SA.cols = Lp;
+        if (j == 1) {
+            SA.X = A->data; SA.ld = A->stride_words; SA.bs = 0; SA.vrows = m; SA.vcols = l;
+        } else {
+            SA.X = reinterpret_cast<const uint64_t *>(scratch + p.offA[j - 1]);
+            SA.ld = p.ldA[j - 1]; SA.bs = p.slabA[j - 1]; SA.vrows = Mp; SA.vcols = Lp;
+        }
+        SA.out = reinterpret_cast<uint64_t *>(scratch + p.offA[j]);
+        SA.cld = p.ldA[j]; SA.cbs = p.slabA[j];
+        int rc = sw_split_launch(SA, s);
+        if (rc) return rc;
+
+        SplitLaunch SB;
+        SB.nparent = (int)cnt;
+        if (tc) {
+            // right factor held transposed (Np x Lp): quadrant NE of B^T is
+            // (B_SW)^T and SW is (B_NE)^T; side 2 swaps their roles
+            SB.side = 2; SB.rows = Np; SB.cols = Lp;
+            if (j == 1) {
+                SB.X = Bsrc; SB.ld = ldBsrc; SB.bs = 0; SB.vrows = n; SB.vcols = l;
+            } else {
+                SB.X = reinterpret_cast<const uint64_t *>(scratch + p.offB[j - 1]);
+                SB.ld = p.ldB[j - 1]; SB.bs = p.slabB[j - 1]; SB.vrows = Np; SB.vcols = Lp;
+            }
+        } else {
+            SB.side = 1; SB.rows = Lp; SB.cols = Np;
+            if (j == 1) {
+                SB.X = B->data; SB.ld = B->stride_words; SB.bs = 0; SB.vrows = l; SB.vcols = n;
+            } else {
+                SB.X = reinterpret_cast<const uint64_t *>(scratch + p.offB[j - 1]);
+                SB.ld = p.ldB[j - 1]; SB.bs = p.slabB[j - 1]; SB.vrows = Lp; SB.vcols = Np;
+            }
+        }
+        SB.out = reinterpret_cast<uint64_t *>(scratch + p.offB[j]);
+        SB.cld = p.ldB[j]; SB.cbs = p.slabB[j];
+        rc = sw_split_launch(SB, s);
+        if (rc) return rc;
+        cnt *= 7;
+    }
+    // all 7^d leaf products in one launch of the base case
+    {
+        const int64_t Md = p.M >> d, Ld = p.L >> d, Nd = p.N >> d;
+        int rc = run_base(p, reinterpret_cast<const uint64_t *>(scratch + p.offA[d]), p.ldA[d], p.slabA[d],
+                          reinterpret_cast<const uint64_t *>(scratch + p.offB[d]), p.ldB[d], p.slabB[d],
+                          reinterpret_cast<uint64_t *>(scratch + p.offP[d]), p.ldP[d], p.slabP[d], Md, Ld,
+                          Nd, (int)cnt, 0, s);
+        if (rc) return rc;
+    }
+    // bottom-up: the 7 final additions of Algorithm 4, Augment and Stack
+    for (int j = d; j >= 1; --j) {
+        cnt /= 7;
+        const int64_t Mp = p.M >> (j - 1), Np = p.N >> (j - 1);
+        CombineLaunch CL;
+        CL.P = reinterpret_cast<const uint64_t *>(scratch + p.offP[j]);
+        CL.pld = p.ldP[j]; CL.pbs = p.slabP[j];
+        CL.rows = Mp; CL.cols = Np; CL.nparent = (int)cnt;
+        if (j == 1) {
+            CL.X = C->data; CL.ld = C->stride_words; CL.bs = 0; CL.vrows = m; CL.vcols = n;
+            CL.accumulate = accumulate;
+        } else {
+            CL.X = reinterpret_cast<uint64_t *>(scratch + p.offP[j - 1]);
+            CL.ld = p.ldP[j - 1]; CL.bs = p.slabP[j - 1]; CL.vrows = Mp; CL.vcols = Np;
+            CL.accumulate = 0;
+        }
+        int rc = sw_combine_launch(CL, s);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+size_t staged_bytes(const gf2_mat *M)
+{
+    return (size_t)(M->rows * even_up(words_of(M->cols))) * 8;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void gf2_default_opts(gf2_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->base = GF2_BASE_AUTO;
+    o->depth = -1;
+}
+
+const char *gf2_strerror(int status)
+{
+    switch (status) {
+    case GF2_OK: return "ok";
+    case GF2_EINVAL: return "invalid argument (null pointer, negative or mismatched dimensions, bad option)";
+    case GF2_EALIAS: return "output overlaps an input";
+    case GF2_ELAYOUT: return "bad layout (stride below ceil(cols/64), odd stride, or data not 16-byte aligned)";
+    case GF2_ENOMEM: return "out of memory";
+    case GF2_ECUDA: return "CUDA error";
+    case GF2_ETIMEOUT: return "device-side wait timed out";
+    case GF2_EUNSUPPORTED: return "unsupported option for this shape or device";
+    case GF2_EMISMATCH: return "verification failed";
+    default: return "unknown status";
+    }
+}
+
+int gf2_alloc(gf2_mat *M, int64_t rows, int64_t cols)
+{
+    if (!M || rows < 0 || cols < 0) return GF2_EINVAL;
+    memset(M, 0, sizeof(*M));
+    M->rows = rows;
+    M->cols = cols;
+    M->stride_words = even_up(words_of(cols));
+    int dev = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    M->device = dev;
+    if (rows == 0 || cols == 0) return GF2_OK;
+    void *p = nullptr;
+    const size_t bytes = (size_t)(rows * M->stride_words) * 8;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        M->data = nullptr;
+        return GF2_ENOMEM;
+    }
+    if (cudaMemset(p, 0, bytes) != cudaSuccess) {
+        cudaFree(p);
+        return GF2_ECUDA;
+    }
+    M->data = static_cast<uint64_t *>(p);
+    return GF2_OK;
+}
+
+int gf2_free(gf2_mat *M)
+{
+    if (!M) return GF2_EINVAL;
+    if (M->data) {
+        if (M->device == GF2_HOST) return GF2_EINVAL;
+        GF2_CUDA_TRY(cudaFree(M->data));
+    }
+    M->data = nullptr;
+    return GF2_OK;
+}
+
+int64_t gf2_scratch_bytes(int64_t m, int64_t l, int64_t n, const gf2_opts *opts)
+{
+    const gf2_opts o = resolve(opts);
+    if (m < 0 || l < 0 || n < 0 || check_opts(o)) return GF2_EINVAL;
+    Plan p;
+    const int rc = make_plan(m, l, n, o, &p);
+    if (rc) return rc;
+    return (int64_t)p.bytes;
+}
+
+int gf2_describe_plan(int64_t m, int64_t l, int64_t n, const gf2_opts *opts, char *buf, int32_t cap)
+{
+    if (!buf || cap <= 0) return GF2_EINVAL;
+    const gf2_opts o = resolve(opts);
+    if (m < 0 || l < 0 || n < 0) return GF2_EINVAL;
+    int rc = check_opts(o);
+    if (rc) return rc;
+    Plan p;
+    rc = make_plan(m, l, n, o, &p);
+    if (rc) return rc;
+    std::string t = plan_text(p);
+    if (o.base != GF2_BASE_TC_FP8 && m > 0 && n > 0) {
+        int k = o.k, tt = o.t, bm = 0, ks = 0;
+        const int d = p.depth;
+        int batch = 1;
+        for (int j = 0; j < d; ++j) batch *= 7;
+        m4rm_pick(p.M >> d, p.L >> d, p.N >> d, batch, &k, &tt, &bm, &ks);
+        char extra[128];
+        snprintf(extra, sizeof extra, " m4rm_k=%d m4rm_t=%d tile_rows=%d ksplit=%d", k, tt, bm, ks);
+        t += extra;
+    }
+    snprintf(buf, (size_t)cap, "%s", t.c_str());
+    return GF2_OK;
+}
+
+int gf2_reserve_scratch(int64_t bytes, void *stream)
+{
+    if (bytes < 0) return GF2_EINVAL;
+    void *p = nullptr;
+    return arena_get(static_cast<cudaStream_t>(stream), (size_t)bytes, &p);
+}
+
+int gf2_release_scratch(void)
+{
+    int dev = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_arena_mu);
+    GF2_CUDA_TRY(cudaDeviceSynchronize());
+    for (auto it = g_arenas.begin(); it != g_arenas.end();) {
+        if (it->first.first == dev) {
+            if (it->second.ptr) cudaFree(it->second.ptr);
+            it = g_arenas.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return GF2_OK;
+}
+
+int64_t gf2_launch_count(void) { return (int64_t)gf2::launch_count(); }
+
+int gf2_profile_enable(int32_t on) { return gf2::profile_enable(on); }
+
+int gf2_profile_read(int32_t family, double *ms, int64_t *launches)
+{
+    long long n = 0;
+    const int rc = gf2::profile_read(family, ms, &n);
+    if (launches) *launches = (int64_t)n;
+    return rc;
+}
+
+const char *gf2_profile_name(int32_t family)
+{
+    static const char *names[PF_COUNT] = {"m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose",
+                                          "random", "freivalds", "make_table", "batched"};
+    if (family < 0 || family >= PF_COUNT) return nullptr;
+    return names[family];
+}
+
+int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts, void *stream)
+{
+    int rc;
+    if ((rc = check_mat(A)) || (rc = check_mat(B)) || (rc = check_mat(C))) return rc;
+    if (A->cols != B->rows || C->rows != A->rows || C->cols != B->cols) return GF2_EINVAL;
+    const gf2_opts o = resolve(opts);
+    if ((rc = check_opts(o))) return rc;
+    if (overlaps(C, A) || overlaps(C, B)) return GF2_EALIAS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    const gf2_mat *mats[3] = {A, B, C};
+    for (const gf2_mat *M : mats)
+        if (M->device != GF2_HOST && M->device != dev && M->rows && M->cols) return GF2_EINVAL;
+
+    const int64_t m = A->rows, l = A->cols, n = B->cols;
+    Plan p;
+    if ((rc = make_plan(m, l, n, o, &p))) return rc;
+
+    const bool hA = A->device == GF2_HOST, hB = B->device == GF2_HOST, hC = C->device == GF2_HOST;
+    size_t total = p.bytes;
+    size_t offA = total, offB = 0, offC = 0;
+    if (hA) { offA = total; total += (staged_bytes(A) + 255) & ~(size_t)255; }
+    if (hB) { offB = total; total += (staged_bytes(B) + 255) & ~(size_t)255; }
+    if (hC) { offC = total; total += (staged_bytes(C) + 255) & ~(size_t)255; }
+    void *scratch = nullptr;
+    if ((rc = arena_get(s, total, &scratch))) return rc;
+    char *base = static_cast<char *>(scratch);
+
+    gf2_mat dA = *A, dB = *B, dC = *C;
+    if (hA && m && l) {
+        dA.data = reinterpret_cast<uint64_t *>(base + offA);
+        dA.stride_words = even_up(words_of(l));
+        dA.device = dev;
+        GF2_CUDA_TRY(cudaMemcpy2DAsync(dA.data, dA.stride_words * 8, A->data, A->stride_words * 8,
+                                       words_of(l) * 8, m, cudaMemcpyHostToDevice, s));
+    }
+    if (hB && l && n) {
+        dB.data = reinterpret_cast<uint64_t *>(base + offB);
+        dB.stride_words = even_up(words_of(n));
+        dB.device = dev;
+        GF2_CUDA_TRY(cudaMemcpy2DAsync(dB.data, dB.stride_words * 8, B->data, B->stride_words * 8,
+                                       words_of(n) * 8, l, cudaMemcpyHostToDevice, s));
+    }
+    if (hC && m && n) {
+        dC.data = reinterpret_cast<uint64_t *>(base + offC);
+        dC.stride_words = even_up(words_of(n));
+        dC.device = dev;
+        if (o.accumulate)
+            GF2_CUDA_TRY(cudaMemcpy2DAsync(dC.data, dC.stride_words * 8, C->data, C->stride_words * 8,
+                                           words_of(n) * 8, m, cudaMemcpyHostToDevice, s));
+    }
+    rc = mul_device(&dC, &dA, &dB, p, o.accumulate, base, s);
+    if (rc) return rc;
+    if (hC && m && n) {
+        GF2_CUDA_TRY(cudaMemcpy2DAsync(C->data, C->stride_words * 8, dC.data, dC.stride_words * 8,
+                                       words_of(n) * 8, m, cudaMemcpyDeviceToHost, s));
+    }
+    if (hA || hB || hC) GF2_CUDA_TRY(cudaStreamSynchronize(s));
+    return GF2_OK;
+}
+
+int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[],
+                    int32_t count, const gf2_opts *opts, void *stream)
+{
+    if (count < 0 || (count > 0 && (!C || !A || !B))) return GF2_EINVAL;
+    const gf2_opts o = resolve(opts);
+    int rc = check_opts(o);
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) {
+        if ((rc = check_mat(A[i])) || (rc = check_mat(B[i])) || (rc = check_mat(C[i]))) return rc;
+        if (A[i]->cols != B[i]->rows || C[i]->rows != A[i]->rows || C[i]->cols != B[i]->cols)
+            return GF2_EINVAL;
+        if (A[i]->device == GF2_HOST || B[i]->device == GF2_HOST || C[i]->device == GF2_HOST)
+            return GF2_EINVAL;
+        if (overlaps(C[i], A[i]) || overlaps(C[i], B[i])) return GF2_EALIAS;
+    }
+    for (int i = 0; i < count; ++i) {
+        rc = gf2_mul(C[i], A[i], B[i], &o, stream);
+        if (rc) return rc;
+    }
+    return GF2_OK;
+}
+
+int gf2_sw_split(uint64_t *out, int64_t slab_words, const gf2_mat *X, int32_t side, void *stream)
+{
+    int rc = check_mat(X);
+    if (rc) return rc;
+    if (!out || side < 0 || side > 2) return GF2_EINVAL;
+    if ((X->rows & 1) || (X->cols % 128)) return GF2_EINVAL;
+    const int64_t cld = even_up(X->cols / 128);
+    if (slab_words < (X->rows / 2) * cld || !aligned16(out) || (slab_words & 1)) return GF2_ELAYOUT;
+    if (X->rows == 0 || X->cols == 0) return GF2_OK;
+    if ((X->cols / 128) & 1) return GF2_EUNSUPPORTED;   // quadrants must be whole 16-byte chunks
+    SplitLaunch L;
+    L.X = X->data; L.ld = X->stride_words; L.bs = 0;
+    L.rows = X->rows; L.cols = X->cols; L.vrows = X->rows; L.vcols = X->cols;
+    L.out = out; L.cld = cld; L.cbs = slab_words; L.nparent = 1; L.side = side;
+    return sw_split_launch(L, static_cast<cudaStream_t>(stream));
+}
+
+int gf2_sw_combine(gf2_mat *C, const uint64_t *P, int64_t slab_words, void *stream)
+{
+    int rc = check_mat(C);
+    if (rc) return rc;
+    if (!P || (C->rows & 1) || (C->cols % 128)) return GF2_EINVAL;
+    const int64_t pld = even_up(C->cols / 128);
+    if (slab_words < (C->rows / 2) * pld || !aligned16(P) || (slab_words & 1)) return GF2_ELAYOUT;
+    if (C->rows == 0 || C->cols == 0) return GF2_OK;
+    if ((C->cols / 128) & 1) return GF2_EUNSUPPORTED;
+    CombineLaunch L;
+    L.P = P; L.pld = pld; L.pbs = slab_words;
+    L.X = C->data; L.ld = C->stride_words; L.bs = 0;
+    L.rows = C->rows; L.cols = C->cols; L.vrows = C->rows; L.vcols = C->cols;
+    L.nparent = 1; L.accumulate = 0;
+    return sw_combine_launch(L, static_cast<cudaStream_t>(stream));
+}
+
+int gf2_make_table(gf2_mat *T, const gf2_mat *B, int64_t r0, int32_t k, void *stream)
+{
+    int rc;
+    if ((rc = check_mat(T)) || (rc = check_mat(B))) return rc;
+    if (k < 1 || k > 10 || r0 < 0) return GF2_EINVAL;
+    if (T->rows != ((int64_t)1 << k) || T->cols != B->cols) return GF2_EINVAL;
+    if (overlaps(T, B)) return GF2_EALIAS;
+    DMat Td{T->data, T->rows, T->cols, T->stride_words};
+    DMat Bd{B->data, B->rows, B->cols, B->stride_words};
+    return make_table_launch(Td, Bd, r0, k, static_cast<cudaStream_t>(stream));
+}
+
+int gf2_random(gf2_mat *M, uint64_t seed, double p, void *stream)
+{
+    int rc = check_mat(M);
+    if (rc) return rc;
+    if (!(p >= 0.0 && p <= 1.0)) return GF2_EINVAL;
+    if (M->device == GF2_HOST) return GF2_EINVAL;
+    DMat D{M->data, M->rows, M->cols, M->stride_words};
+    return random_launch(D, seed, p, static_cast<cudaStream_t>(stream));
+}
+
+int gf2_transpose(gf2_mat *T, const gf2_mat *X, void *stream)
+{
+    int rc;
+    if ((rc = check_mat(T)) || (rc = check_mat(X))) return rc;
+    if (T->rows != X->cols || T->cols != X->rows) return GF2_EINVAL;
+    if (overlaps(T, X)) return GF2_EALIAS;
+    DMat Td{T->data, T->rows, T->cols, T->stride_words};
+    DMat Xd{X->data, X->rows, X->cols, X->stride_words};
+    return transpose_launch(Td, Xd, static_cast<cudaStream_t>(stream));
+}
+
+int gf2_freivalds(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, uint64_t seed,
+                  int64_t *mismatched_rows, void *stream)
+{
+    int rc;
+    if (!mismatched_rows) return GF2_EINVAL;
+    if ((rc = check_mat(A)) || (rc = check_mat(B)) || (rc = check_mat(C))) return rc;
+    if (A->cols != B->rows || C->rows != A->rows || C->cols != B->cols) return GF2_EINVAL;
+    if (A->device == GF2_HOST || B->device == GF2_HOST || C->device == GF2_HOST) return GF2_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t m = A->rows, l = A->cols, n = B->cols;
+    *mismatched_rows = 0;
+    if (m == 0) return GF2_OK;
+    const int64_t ldxn = even_up(words_of(n)), ldxl = even_up(words_of(l));
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t a = off; off += (bytes + 255) & ~(size_t)255; return a; };
+    const size_t oX = take((size_t)std::max<int64_t>(n, 1) * 8);
+    const size_t oXT = take((size_t)(64 * ldxn) * 8);
+    const size_t oY1 = take((size_t)std::max<int64_t>(l, 1) * 8);
+    const size_t oY1T = take((size_t)(64 * ldxl) * 8);
+    const size_t oY2 = take((size_t)m * 8);
+    const size_t oY3 = take((size_t)m * 8);
+    const size_t oCnt = take(8);
+    void *scr = nullptr;
+    if ((rc = arena_get(s, off, &scr))) return rc;
+    char *b = static_cast<char *>(scr);
+    uint64_t *X = reinterpret_cast<uint64_t *>(b + oX), *XT = reinterpret_cast<uint64_t *>(b + oXT);
+    uint64_t *Y1 = reinterpret_cast<uint64_t *>(b + oY1), *Y1T = reinterpret_cast<uint64_t *>(b + oY1T);
+    uint64_t *Y2 = reinterpret_cast<uint64_t *>(b + oY2), *Y3 = reinterpret_cast<uint64_t *>(b + oY3);
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b + oCnt);
+    GF2_CUDA_TRY(cudaMemsetAsync(cnt, 0, 8, s));
+    GF2_CUDA_TRY(cudaMemsetAsync(Y1T, 0, (size_t)(64 * ldxl) * 8, s));
+    GF2_CUDA_TRY(cudaMemsetAsync(XT, 0, (size_t)(64 * ldxn) * 8, s));
+    if ((rc = seeded_words_launch(X, n, seed, s))) return rc;
+    // XT = X^T (64 x n), X seen as an n x 64 matrix with one word per row
+    if (n > 0 && (rc = transpose_launch(DMat{XT, 64, n, ldxn}, DMat{X, n, 64, 1}, s))) return rc;
+    if (l > 0) {
+        // Y1 = B X (l words), Y1T = Y1^T
+        if ((rc = matvec64_launch(B->data, l, n, B->stride_words, XT, Y1, s))) return rc;
+        if ((rc = transpose_launch(DMat{Y1T, 64, l, ldxl}, DMat{Y1, l, 64, 1}, s))) return rc;
+    }
+    // Y2 = A (B X), Y3 = C X
+    if ((rc = matvec64_launch(A->data, m, l, A->stride_words, Y1T, Y2, s))) return rc;
+    if ((rc = matvec64_launch(C->data, m, n, C->stride_words, XT, Y3, s))) return rc;
+    if ((rc = xor_count_launch(Y2, Y3, m, cnt, s))) return rc;
+    unsigned long long h = 0;
+    GF2_CUDA_TRY(cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, s));
+    GF2_CUDA_TRY(cudaStreamSynchronize(s));
+    *mismatched_rows = (int64_t)h;
+    return GF2_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,481 @@
+// m4rm.cu -- Method of the Four Russians base case on packed words (sm_103a).
+//
+// Section 3 (Algorithm 1): split A into stripes of k columns and B into
+// stripes of k rows; tabulate all 2^k combinations of the k rows of a B
+// stripe (MakeTable), then every row of A reads its k bits of the stripe
+// (ReadBits) and adds that table row to its row of C (AddRowFromTable).
+// Section 3.2 (Algorithm 2): the table is rebuilt per block of rows so that
+// the rows being updated stay in fast memory.  Section 3.3 (Algorithm 3): t
+// tables cover t*k rows of B per pass and each row of C receives t table
+// rows per pass.
+//
+// GB300 mapping:
+//  * one CTA owns a tile of BM rows x 1024 columns of C, held in REGISTERS
+//    for the whole K loop (the analogue of the cache-friendly block);
+//  * the t tables of one pass live in SHARED MEMORY, 128 bytes per table row;
+//    B rows of the next pass are staged by cp.async while the current pass
+//    runs;
+//  * a table is built by the Gray-code walk of Section 3.1 in registers: a
+//    thread holds the combination of the high bits of the index and walks
+//    the low 4 bits in Gray order, one row addition (4 x 32-bit XOR) per new
+//    entry, so the whole table costs 2^k - 1 row additions as in the paper;
+//  * lookups: 8 lanes share one C row (16 bytes = 128 columns each), so a
+//    warp updates 4 rows per 128-bit shared-memory load; all accesses of a
+//    quarter-warp fall in one 128-byte table row (conflict free).
+//
+// Table index convention: bit j of the index selects row (stripe start + j),
+// and the index is read least-significant-bit first from the packed row of A
+// (column c is bit c % 64 of its word).  The paper's ReadBits reads the
+// stripe most-significant-bit first; the order is internal to a table and
+// does not change the product.
+#include "common.cuh"
+
+#include <mutex>
+#include <type_traits>
+
+namespace gf2 {
+namespace {
+
+constexpr int LPR = 8;          // lanes per C row
+constexpr int TILE_WORDS = 16;  // 64-bit words of C per tile row (1024 columns)
+
+struct Params {
+    const uint64_t *A; int64_t lda, bsA;
+    const uint64_t *B; int64_t ldb, bsB;
+    uint64_t *C; int64_t ldc, bsC;
+    int64_t m, l, n;
+    int ksplit;
+    int64_t groups_per_split;
+    int mode;                   // 0: store, 1: C ^= (plain), 2: atomic XOR
+};
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int sz = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__host__ __device__ constexpr int ctz_c(int s) { return (s & 1) ? 0 : 1 + ctz_c(s >> 1); }
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int sz = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint4 x4(uint4 a, uint4 b)
+{
+    return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
+}
+__device__ __forceinline__ uint4 and4(uint4 a, uint4 m)
+{
+    return make_uint4(a.x & m.x, a.y & m.y, a.z & m.z, a.w & m.w);
+}
+
+// Steps s = S .. 2^LOB - 1 of the Gray-code walk of Section 3.1: entry
+// gray(s) = gray(s-1) + (row ctz(s)), one row addition per entry.  A template
+// recursion keeps every register index a compile-time constant.
+template <int S, int LOB>
+struct GrayWalk {
+    static __device__ __forceinline__ void run(uint4 &v, const uint4 (&lo)[LOB], uint4 *T, int base)
+    {
+        constexpr int j = ctz_c(S);
+        v = x4(v, lo[j]);
+        T[(base | (S ^ (S >> 1))) * LPR] = v;
+        GrayWalk<S + 1, LOB>::run(v, lo, T, base);
+    }
+};
+template <int LOB>
+struct GrayWalk<(1 << LOB), LOB> {
+    static __device__ __forceinline__ void run(uint4 &, const uint4 (&)[LOB], uint4 *, int) {}
+};
+
+// Build NT tables of 2^KB rows from KB*NT staged B rows (each 8 x 16 bytes),
+// one 16-byte column chunk per item (Section 3.1 Gray-code walk over the low
+// bits of the index, high bits combined directly).  `cmask` masks the
+// thread's column chunk (chunk == tid % 8 for every item of this thread).
+template <int KB, int NT, int NTH>
+__device__ __forceinline__ void build_tables(uint4 *tab, const uint4 *stg, int tid, uint4 cmask)
+{
+    constexpr int LOB = KB < 4 ? KB : 4;
+    constexpr int HIB = KB - LOB;
+    constexpr int TROWS = 1 << KB;
+    constexpr int ITEMS = NT * (1 << HIB) * LPR;
+#pragma unroll 1
+    for (int it = tid; it < ITEMS; it += NTH) {
+        const int c = it & 7;
+        const int hi = (it >> 3) & ((1 << HIB) - 1);
+        const int ti = it >> (3 + HIB);
+        const uint4 *S = stg + ti * KB * LPR + c;     // row j of the stripe at S[j*8]
+        uint4 lo[LOB];
+#pragma unroll
+        for (int j = 0; j < LOB; ++j) lo[j] = and4(S[j * LPR], cmask);
+        uint4 v = make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int j = 0; j < HIB; ++j)
+            if ((hi >> j) & 1) v = x4(v, and4(S[(LOB + j) * LPR], cmask));
+        uint4 *T = tab + ti * TROWS * LPR + c;        // entry x at T[x*8]
+        const int base = hi << LOB;
+        T[base * LPR] = v;
+        GrayWalk<1, LOB>::run(v, lo, T, base);
+    }
+}
+
+template <int KB, int NT, int R, int NWARP>
+__global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
+{
+    constexpr int NTH = NWARP * 32;
+    constexpr int KG = KB * NT;          // rows of B per pass = bits of each A row per pass
+    constexpr int TROWS = 1 << KB;
+    constexpr int BM = NWARP * 4 * R;
+    constexpr unsigned IMASK = (1u << KB) - 1u;
+    static_assert(KG <= 64, "a pass reads at most 64 bits of a row of A");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);        // NT * TROWS * 8
+    uint4 *stg = tab + NT * TROWS * LPR;                       // 2 * KG * 8   (B rows of a pass)
+    uint4 *sta = stg + 2 * KG * LPR;                           // 2 * BM       (A words of a pass)
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int chunk = lane & 7;
+    const int64_t w0 = (int64_t)blockIdx.x * TILE_WORDS;
+    const int64_t row0 = (int64_t)blockIdx.y * BM;
+    const int bidx = blockIdx.z / P.ksplit;
+    const int split = blockIdx.z % P.ksplit;
+
+    const uint64_t *A = P.A + (int64_t)bidx * P.bsA;
+    const uint64_t *B = P.B + (int64_t)bidx * P.bsB;
+    uint64_t *C = P.C + (int64_t)bidx * P.bsC;
+
+    const int64_t nW = words_of(P.n);
+    const int64_t lW = words_of(P.l);
+    const int groups = (int)((P.l + KG - 1) / KG);
+    const int g_begin = split * (int)P.groups_per_split;
+    const int g_end = min(groups, g_begin + (int)P.groups_per_split);
+
+    const int64_t cw = w0 + 2 * chunk;
+    const uint64_t cm0 = word_mask(cw, P.n), cm1 = word_mask(cw + 1, P.n);
+    const uint4 cmask = make_uint4((uint32_t)cm0, (uint32_t)(cm0 >> 32), (uint32_t)cm1,
+                                   (uint32_t)(cm1 >> 32));
+
+    const int trow = warp * 4 * R + (lane >> 3);               // tile row of row-group r: trow + 4r
+
+    uint4 acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+
+    // Stage pass g: its KG rows of B (tile columns) and the 1-2 words of each
+    // tile row of A that hold columns g*KG .. g*KG+KG-1.
+    auto issue_stage = [&](int g, int buf) {
+#pragma unroll 1
+        for (int i = tid; i < KG * LPR; i += NTH) {
+            const int rr = i >> 3, cc = i & 7;
+            const int64_t brow = (int64_t)g * KG + rr;
+            const int64_t bw = w0 + 2 * cc;
+            const bool valid = (brow < P.l) && (bw < nW);
+            cp_async16(&stg[buf * KG * LPR + i], valid ? (B + brow * P.ldb + bw) : B, valid);
+        }
+        const int64_t kb = (int64_t)g * KG;
+        const int64_t wa = kb >> 6;
+        const bool two = ((kb & 63) + KG > 64) && (wa + 1 < lW);
+#pragma unroll 1
+        for (int i = tid; i < BM; i += NTH) {
+            const int64_t row = row0 + i;
+            const bool valid = row < P.m;
+            const uint64_t *src = A + (valid ? row * P.lda + wa : 0);
+            uint4 *dst = &sta[buf * BM + i];
+            cp_async8(dst, src, valid);
+            if (two) cp_async8(reinterpret_cast<char *>(dst) + 8, src + 1, valid);
+        }
+        cp_async_commit();
+    };
+
+    if (g_begin < g_end) issue_stage(g_begin, 0);
+
+#pragma unroll 1
+    for (int g = g_begin; g < g_end; ++g) {
+        const int buf = (g - g_begin) & 1;
+        cp_async_wait_all();
+        __syncthreads();                       // staged rows visible; previous lookups done
+        if (g + 1 < g_end) issue_stage(g + 1, buf ^ 1);
+        build_tables<KB, NT, NTH>(tab, stg + buf * KG * LPR, tid, cmask);
+        __syncthreads();                       // tables complete
+        // ReadBits + AddRowFromTable for NT tables (Algorithms 1 and 3).
+        const int64_t kb = (int64_t)g * KG;
+        const int64_t wa = kb >> 6;
+        const int sh = (int)(kb & 63);
+        const uint64_t mlo = word_mask(wa, P.l);
+        const uint64_t mhi = (sh + KG > 64) ? word_mask(wa + 1, P.l) : 0ull;
+        const uint4 *arow = sta + buf * BM + trow;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint2 aw = *reinterpret_cast<const uint2 *>(&arow[4 * r]);
+            const uint64_t lo = ((uint64_t)aw.y << 32 | aw.x) & mlo;
+            uint64_t bits = lo >> sh;
+            if (sh + KG > 64) {
+                const uint2 aw2 = reinterpret_cast<const uint2 *>(&arow[4 * r])[1];
+                bits |= (((uint64_t)aw2.y << 32 | aw2.x) & mhi) << (64 - sh);
+            }
+            uint4 a = acc[r];
+#pragma unroll
+            for (int ti = 0; ti < NT; ++ti) {
+                const unsigned x = (unsigned)(bits >> (ti * KB)) & IMASK;
+                a = x4(a, tab[(ti * TROWS + (int)x) * LPR + chunk]);
+            }
+            acc[r] = a;
+            // keeps the compiler from hoisting the loads of later row-groups:
+            // t loads in flight per warp already saturate shared memory
+            asm volatile("" ::: "memory");
+        }
+    }
+
+    // write the C tile: one loop per mode so that the row loop stays simple
+    if (cw < nW) {
+        const int64_t first = row0 + trow;
+        const int64_t left = P.m - first;               // rows of this thread: first + 4r, r < R
+        const int nrows = left <= 0 ? 0 : (left < 4 * R ? (int)left : 4 * R);
+        uint64_t *cr = C + first * P.ldc + cw;
+        const int64_t step = 4 * P.ldc;
+        if (P.mode == 0 && cw + 1 < nW) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (4 * r < nrows)
+                    *reinterpret_cast<uint4 *>(cr + r * step) = and4(acc[r], cmask);
+            }
+        } else {
+            const bool two = (cw + 1 < nW);
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+                if (4 * r >= nrows) break;
+                uint4 a = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                for (int q = 0; q < R; ++q)
+                    if (q == r) a = acc[q];
+                const uint64_t v0 = ((uint64_t)a.y << 32 | a.x) & cm0;
+                const uint64_t v1 = ((uint64_t)a.w << 32 | a.z) & cm1;
+                uint64_t *c = cr + r * step;
+                if (P.mode == 0) {
+                    c[0] = v0;
+                } else if (P.mode == 1) {
+                    c[0] ^= v0;
+                    if (two) c[1] ^= v1;
+                } else {
+                    atomicXor(reinterpret_cast<unsigned long long *>(c), (unsigned long long)v0);
+                    if (two) atomicXor(reinterpret_cast<unsigned long long *>(c + 1), (unsigned long long)v1);
+                }
+            }
+        }
+    }
+}
+
+// Standalone MakeTable (Algorithm 1) into global memory, using the same
+// build routine as the base case: one CTA per 1024-column tile.
+template <int KB>
+__global__ void __launch_bounds__(256) make_table_kernel(DMat T, DMat B, int64_t r0)
+{
+    constexpr int NTH = 256;
+    constexpr int TROWS = 1 << KB;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);
+    uint4 *stg = tab + TROWS * LPR;
+    const int tid = threadIdx.x;
+    const int64_t w0 = (int64_t)blockIdx.x * TILE_WORDS;
+    const int64_t nW = words_of(B.cols);
+    for (int i = tid; i < KB * LPR; i += NTH) {
+        const int rr = i >> 3, cc = i & 7;
+        const int64_t brow = r0 + rr;
+        const int64_t bw = w0 + 2 * cc;
+        const bool valid = (brow < B.rows) && (bw < nW);
+        cp_async16(&stg[i], valid ? (B.p + brow * B.ld + bw) : B.p, valid);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    const int chunk = tid & 7;
+    const int64_t cw = w0 + 2 * chunk;
+    const uint64_t cm0 = word_mask(cw, B.cols), cm1 = word_mask(cw + 1, B.cols);
+    const uint4 cmask = make_uint4((uint32_t)cm0, (uint32_t)(cm0 >> 32), (uint32_t)cm1,
+                                   (uint32_t)(cm1 >> 32));
+    build_tables<KB, 1, NTH>(tab, stg, tid, cmask);
+    __syncthreads();
+    for (int i = tid; i < TROWS * LPR; i += NTH) {
+        const int x = i >> 3, c = i & 7;
+        const int64_t w = w0 + 2 * c;
+        if (w >= nW) continue;
+        const uint4 v = tab[i];
+        uint64_t *dst = T.p + (int64_t)x * T.ld + w;
+        dst[0] = ((uint64_t)v.y << 32) | v.x;
+        if (w + 1 < nW) dst[1] = ((uint64_t)v.w << 32) | v.z;
+    }
+}
+
+using KernelFn = void (*)(Params);
+
+struct Variant {
+    int k, t, bm, nw;     // bits per table, tables per pass, tile rows, warps per CTA
+    KernelFn fn;
+    int smem;
+};
+
+// Tile rows BM = 4 * R * NW.  Tall tiles (BM = 1024) use 8 warps holding
+// 32 row-groups each (128 accumulator registers per thread, no spills).
+template <int KB, int NT, int R, int NW>
+Variant make_variant()
+{
+    constexpr int BM = 4 * R * NW;
+    return Variant{KB, NT, BM, NW, &m4rm_kernel<KB, NT, R, NW>,
+                   (int)(NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16)};
+}
+
+const Variant kVariants[] = {
+    make_variant<8, 4, 32, 8>(), make_variant<8, 2, 32, 8>(), make_variant<7, 8, 32, 8>(),
+    make_variant<6, 8, 32, 8>(), make_variant<9, 2, 32, 8>(), make_variant<10, 1, 32, 8>(),
+    make_variant<5, 8, 32, 8>(), make_variant<4, 8, 32, 8>(),
+    make_variant<8, 4, 16, 16>(),
+    make_variant<8, 4, 4, 16>(), make_variant<6, 8, 4, 16>(), make_variant<4, 8, 4, 16>(),
+    make_variant<8, 4, 1, 16>(), make_variant<6, 8, 1, 16>(), make_variant<4, 8, 1, 16>(),
+};
+
+const Variant *find_variant(int k, int t, int bm)
+{
+    for (const Variant &v : kVariants)
+        if (v.k == k && v.t == t && v.bm == bm) return &v;
+    return nullptr;
+}
+
+}  // namespace
+
+bool m4rm_supported(int k, int t)
+{
+    for (const Variant &v : kVariants)
+        if (v.k == k && v.t == t) return true;
+    return false;
+}
+
+static int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// Row-tile height and (k, t) for a shape: tall tiles (1024 rows) amortise
+// the 2^k-row table over many lookups (table cost / lookup cost = 2^k / BM,
+// Section 3.2's trade-off); small problems take shorter tiles and smaller k
+// so that every SM has work, and split K when even that is not enough.
+void m4rm_pick(int64_t m, int64_t l, int64_t n, int batch, int *k, int *t, int *bm, int *ksplit)
+{
+    const int sms = sm_count();
+    const int64_t tn = (words_of(n) + TILE_WORDS - 1) / TILE_WORDS;
+    const int bms[3] = {1024, 256, 64};
+    int b = 1024;
+    for (int i = 0; i < 3; ++i) {
+        b = bms[i];
+        const int64_t ctas = (int64_t)batch * tn * ((m + b - 1) / b);
+        if (ctas >= 2 * sms) break;
+    }
+    int kk = (b == 1024) ? 8 : (b == 256 ? 6 : 4);
+    int tt = (b == 1024) ? 4 : 8;
+    if (*k > 0 || *t > 0) {
+        if (*k > 0) kk = *k;
+        tt = *t;
+        if (tt <= 0) {
+            tt = 0;
+            for (const Variant &v : kVariants)
+                if (v.k == kk && v.bm == 1024) { tt = v.t; break; }
+        }
+        // keep the requested (k, t); fall back to the tallest tile that has it
+        if (!find_variant(kk, tt, b)) b = 1024;
+    }
+    const int64_t ctas = (int64_t)batch * tn * ((m + b - 1) / b);
+    const int64_t groups = (l + kk * tt - 1) / (kk * tt);
+    int ks = 1;
+    if (ctas < sms && groups > 1) {
+        ks = (int)((sms + ctas - 1) / ctas);
+        if (ks > groups) ks = (int)groups;
+        if (ks > 64) ks = 64;
+    }
+    *k = kk; *t = tt; *bm = b; *ksplit = ks;
+}
+
+int m4rm_launch(const M4rmLaunch &L, cudaStream_t s)
+{
+    if (L.batch <= 0 || L.m <= 0 || L.n <= 0) return GF2_OK;
+    int k = L.k, t = L.t, bm = 1024, ks_auto = 1;
+    m4rm_pick(L.m, L.l, L.n, L.batch, &k, &t, &bm, &ks_auto);
+    if (L.bm > 0) bm = L.bm;
+    int ks = L.ksplit > 0 ? L.ksplit : ks_auto;
+    const Variant *v = find_variant(k, t, bm);
+    if (!v) v = find_variant(k, t, 1024);
+    if (!v) return GF2_EUNSUPPORTED;
+    const int KG = v->k * v->t;
+    const int64_t groups = (L.l + KG - 1) / KG;
+    if (groups <= 1) ks = 1;
+    if (ks > groups && groups > 0) ks = (int)groups;
+    const int64_t gps = groups > 0 ? (groups + ks - 1) / ks : 0;
+    if (groups > 0) ks = (int)((groups + gps - 1) / gps);
+
+    Params P;
+    P.A = L.A; P.lda = L.lda; P.bsA = L.bsA;
+    P.B = L.B; P.ldb = L.ldb; P.bsB = L.bsB;
+    P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
+    P.m = L.m; P.l = L.l; P.n = L.n;
+    P.ksplit = ks;
+    P.groups_per_split = gps;
+    if (ks > 1) {
+        // partial products of the K splits are XORed into C (order-free)
+        if (!L.accumulate) {
+            for (int b = 0; b < L.batch; ++b)
+                GF2_CUDA_TRY(cudaMemset2DAsync(L.C + b * L.bsC, L.ldc * 8, 0,
+                                               (size_t)words_of(L.n) * 8, (size_t)L.m, s));
+        }
+        P.mode = 2;
+    } else {
+        P.mode = L.accumulate ? 1 : 0;
+    }
+    dim3 grid((unsigned)div_up(words_of(L.n), TILE_WORDS), (unsigned)div_up(L.m, v->bm),
+              (unsigned)(L.batch * ks));
+    if (grid.y > 65535u || grid.z > 65535u) return GF2_EUNSUPPORTED;
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        GF2_CUDA_TRY(cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v->smem));
+    }
+    ProfScope ps(PF_M4RM, s);
+    v->fn<<<grid, v->nw * 32, v->smem, s>>>(P);
+    note_launch();
+    return check_launch();
+}
+
+int make_table_launch(DMat T, DMat B, int64_t r0, int k, cudaStream_t s)
+{
+    using Fn = void (*)(DMat, DMat, int64_t);
+    static const Fn fns[11] = {nullptr,
+                               make_table_kernel<1>, make_table_kernel<2>, make_table_kernel<3>,
+                               make_table_kernel<4>, make_table_kernel<5>, make_table_kernel<6>,
+                               make_table_kernel<7>, make_table_kernel<8>, make_table_kernel<9>,
+                               make_table_kernel<10>};
+    if (k < 1 || k > 10) return GF2_EINVAL;
+    if (B.cols <= 0) return GF2_OK;
+    const int smem = (1 << k) * LPR * 16 + k * LPR * 16;
+    GF2_CUDA_TRY(cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((unsigned)div_up(words_of(B.cols), TILE_WORDS));
+    ProfScope ps(PF_TABLE, s);
+    fns[k]<<<grid, 256, smem, s>>>(T, B, r0);
+    note_launch();
+    return check_launch();
+}
+
+}  // namespace gf2
