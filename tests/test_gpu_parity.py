@@ -88,8 +88,8 @@ def test_m4rm_density_09_and_accumulate():
     A, B = inputs(m, l, n, p=0.9)
     ref = oracle.mul_packed(A, B, m, l, n)
     C0 = synth.random_packed(m, n, 5)
-    Cd = to_dev(C0)
-    g.gf2_mul(g.mat(Cd, n), g.mat(to_dev(A), l), g.mat(to_dev(B), n),
+    Cd, Ad, Bd = to_dev(C0), to_dev(A), to_dev(B)     # keep the tensors alive across the call
+    g.gf2_mul(g.mat(Cd, n), g.mat(Ad, l), g.mat(Bd, n),
               g.opts(base=g.GF2_BASE_M4RM, depth=0, accumulate=1))
     torch.cuda.synchronize()
     assert_same_bits(to_host(Cd), ref ^ C0, n, "accumulate")
@@ -194,11 +194,12 @@ def test_make_table_matches_gray_code_table(k):
     B = synth.random_packed(rows, cols, 8)
     T = g.empty(1 << k, cols)
     r0 = 35                              # rows beyond B count as zero when k is large
-    g.gf2_make_table(g.mat(T, cols), g.mat(to_dev(B), cols), r0, k)
+    Bd = to_dev(B)
+    g.gf2_make_table(g.mat(T, cols), g.mat(Bd, cols), r0, k)
     torch.cuda.synchronize()
     Tg = synth.unpack_bits(to_host(T), cols)
     bits = synth.unpack_bits(B, cols)
-    padded = np.zeros((r0 + k, cols), np.uint8)
+    padded = np.zeros((max(rows, r0 + k), cols), np.uint8)
     padded[:rows] = bits
     Tor, adds = oracle.make_table(padded, r0, 0, k)
     assert adds == (1 << k) - 1
@@ -214,7 +215,8 @@ def test_make_table_matches_gray_code_table(k):
 def test_transpose():
     X = synth.random_packed(300, 700, 4)
     T = g.empty(700, 300)
-    g.gf2_transpose(g.mat(T, 300), g.mat(to_dev(X), 700))
+    Xd = to_dev(X)
+    g.gf2_transpose(g.mat(T, 300), g.mat(Xd, 700))
     torch.cuda.synchronize()
     assert np.array_equal(synth.unpack_bits(to_host(T), 300), synth.unpack_bits(X, 700).T)
 
