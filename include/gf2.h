@@ -51,6 +51,7 @@ extern "C" {
 #define GF2_ETIMEOUT     (-6)  /* a bounded device-side wait expired                          */
 #define GF2_EUNSUPPORTED (-7)  /* option not available for this shape or device               */
 #define GF2_EMISMATCH    (-8)  /* verification found C != A B                                 */
+#define GF2_ESCRATCH     (-9)  /* gf2_mul_noalloc: the plan needs more than its fixed scratch  */
 
 #define GF2_HOST (-1)          /* gf2_mat.device value for host memory */
 
@@ -195,6 +196,41 @@ int64_t gf2_launch_count(void);
 int gf2_profile_enable(int32_t on);
 int gf2_profile_read(int32_t family, double *ms, int64_t *launches);
 const char *gf2_profile_name(int32_t family);
+
+/* ---- product without allocation --------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers of this
+ * library that cannot allocate device memory.  Two kinds of caller need it:
+ * code that runs inside a framework which has already reserved nearly all
+ * of the GPU's memory for its own allocator (a cudaMalloc of the scratch
+ * would fail there), and code on a latency-critical path that must not
+ * absorb the device-wide synchronisation that cudaMalloc and cudaFree
+ * imply.
+ *
+ * gf2_mul_noalloc computes exactly what gf2_mul computes (same plan, same
+ * kernels, same options) for device operands, but takes the Strassen-
+ * Winograd temporaries (and the transposed B of the tensor-core base case)
+ * from one fixed buffer of GF2_NOALLOC_SCRATCH_BYTES that lives in the
+ * library's device image: every GPU that loads the library holds that
+ * buffer until the process exits.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The caller still provides A, B and C.
+ *
+ *  - The first call on a device looks up the buffer's device address
+ *    (cudaGetSymbolAddress, once per device, with that device current);
+ *    make that first call before any stream capture.
+ *  - If the plan for these shapes and options needs more scratch than the
+ *    buffer holds, the call launches nothing and returns GF2_ESCRATCH
+ *    (gf2_scratch_bytes gives the need; lower opts->depth to reduce it).
+ *    With 32 MiB, square products fit up to n = 6912 at depth 1 and
+ *    n = 4096 at depth 2; depth 0 needs none with the packed base case.
+ *  - All calls share the one buffer, which keeps the last call's contents
+ *    (every part a call reads is written by that call first).  Calls whose
+ *    work overlaps on the GPU (several streams, or several host threads)
+ *    race on the buffer: serialise them, e.g. on one stream.
+ *  - Host operands (GF2_HOST) are rejected with GF2_EINVAL.
+ */
+#define GF2_NOALLOC_SCRATCH_BYTES ((int64_t)32 << 20)
+int gf2_mul_noalloc(gf2_mat *C, const gf2_mat *A, const gf2_mat *B,
+                    const gf2_opts *opts, void *cuda_stream);
 
 /* Plan that gf2_mul would use for these shapes and options, as text (for
  * logs and tests): writes at most `cap` bytes including the terminating NUL.

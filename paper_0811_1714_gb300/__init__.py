@@ -36,6 +36,9 @@ GF2_ECUDA = -5
 GF2_ETIMEOUT = -6
 GF2_EUNSUPPORTED = -7
 GF2_EMISMATCH = -8
+GF2_ESCRATCH = -9
+#: size of the fixed device buffer used by gf2_mul_noalloc
+GF2_NOALLOC_SCRATCH_BYTES = 32 << 20
 GF2_HOST = -1
 
 GF2_BASE_AUTO = 0
@@ -48,7 +51,7 @@ EXPORTS = (
     "gf2_sw_split", "gf2_sw_combine", "gf2_make_table", "gf2_random", "gf2_transpose",
     "gf2_freivalds", "gf2_scratch_bytes", "gf2_reserve_scratch", "gf2_release_scratch",
     "gf2_launch_count", "gf2_describe_plan", "gf2_profile_enable", "gf2_profile_read",
-    "gf2_profile_name",
+    "gf2_profile_name", "gf2_mul_noalloc",
 )
 
 
@@ -130,6 +133,7 @@ def lib():
                 "gf2_profile_enable": (ctypes.c_int, [i32]),
                 "gf2_profile_read": (ctypes.c_int, [i32, _P(ctypes.c_double), _P(i64)]),
                 "gf2_profile_name": (ctypes.c_char_p, [i32]),
+                "gf2_mul_noalloc": (ctypes.c_int, [_P(Mat), _P(Mat), _P(Mat), _P(Opts), vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -210,6 +214,15 @@ def gf2_mul(C: Mat, A: Mat, B: Mat, options: Opts | None = None, stream=None) ->
     o = ctypes.byref(options) if options is not None else None
     _check(lib().gf2_mul(ctypes.byref(C), ctypes.byref(A), ctypes.byref(B), o, _stream(stream)),
            "gf2_mul")
+
+
+def gf2_mul_noalloc(C: Mat, A: Mat, B: Mat, options: Opts | None = None, stream=None) -> None:
+    """gf2_mul without any device allocation: the temporaries come from the
+    library's fixed buffer (GF2_NOALLOC_SCRATCH_BYTES).  For callers that
+    cannot allocate device memory; calls that overlap on the GPU race."""
+    o = ctypes.byref(options) if options is not None else None
+    _check(lib().gf2_mul_noalloc(ctypes.byref(C), ctypes.byref(A), ctypes.byref(B), o,
+                                 _stream(stream)), "gf2_mul_noalloc")
 
 
 def gf2_mul_batched(C: list, A: list, B: list, options: Opts | None = None, stream=None) -> None:

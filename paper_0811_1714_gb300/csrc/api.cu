@@ -343,6 +343,37 @@ size_t staged_bytes(const gf2_mat *M)
 
 }  // namespace
 
+namespace gf2 {
+
+// gf2_mul for device operands with caller-owned scratch (no allocation):
+// the checks of gf2_mul, the same plan, then the device path on `scratch`.
+int mul_with_scratch(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts,
+                     void *scratch, size_t scratch_bytes, void *stream)
+{
+    int rc;
+    if ((rc = check_mat(A)) || (rc = check_mat(B)) || (rc = check_mat(C))) return rc;
+    if (A->cols != B->rows || C->rows != A->rows || C->cols != B->cols) return GF2_EINVAL;
+    const gf2_opts o = resolve(opts);
+    if ((rc = check_opts(o))) return rc;
+    if (overlaps(C, A) || overlaps(C, B)) return GF2_EALIAS;
+    int dev = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    const gf2_mat *mats[3] = {A, B, C};
+    for (const gf2_mat *M : mats)
+        if (M->rows && M->cols && M->device != dev) return GF2_EINVAL;
+    Plan p;
+    if ((rc = make_plan(A->rows, A->cols, B->cols, o, &p))) return rc;
+    if (p.bytes > scratch_bytes) return GF2_ESCRATCH;
+    return mul_device(C, A, B, p, o.accumulate, static_cast<char *>(scratch),
+                      static_cast<cudaStream_t>(stream));
+}
+
+}  // namespace gf2
+
+namespace {
+
+}  // namespace
+
 // ====================================================================== C ABI
 extern "C" {
 
@@ -366,6 +397,7 @@ const char *gf2_strerror(int status)
     case GF2_ETIMEOUT: return "device-side wait timed out";
     case GF2_EUNSUPPORTED: return "unsupported option for this shape or device";
     case GF2_EMISMATCH: return "verification failed";
+    case GF2_ESCRATCH: return "the plan needs more scratch than the fixed no-allocation buffer holds";
     default: return "unknown status";
     }
 }
