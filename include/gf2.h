@@ -183,6 +183,13 @@ int gf2_release_scratch(void);
 /* Number of kernels this library has launched in this process (all devices). */
 int64_t gf2_launch_count(void);
 
+/* gf2_device_status: waits for `cuda_stream`, then reads and clears the
+ * device status word of the tensor-core base case.  Returns GF2_OK, or
+ * GF2_ETIMEOUT when one of its bounded waits expired since the last read
+ * (its kernels then stop early and the product is not valid).
+ */
+int gf2_device_status(void *cuda_stream);
+
 /* ---- device-time accounting ----------------------------------------------
  * gf2_profile_enable(1) clears the counters and starts bracketing every
  * kernel launch of the library with CUDA events on its stream; (0) stops.

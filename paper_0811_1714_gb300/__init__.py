@@ -51,7 +51,7 @@ EXPORTS = (
     "gf2_sw_split", "gf2_sw_combine", "gf2_make_table", "gf2_random", "gf2_transpose",
     "gf2_freivalds", "gf2_scratch_bytes", "gf2_reserve_scratch", "gf2_release_scratch",
     "gf2_launch_count", "gf2_describe_plan", "gf2_profile_enable", "gf2_profile_read",
-    "gf2_profile_name", "gf2_mul_noalloc",
+    "gf2_profile_name", "gf2_mul_noalloc", "gf2_device_status",
 )
 
 
@@ -134,6 +134,7 @@ def lib():
                 "gf2_profile_read": (ctypes.c_int, [i32, _P(ctypes.c_double), _P(i64)]),
                 "gf2_profile_name": (ctypes.c_char_p, [i32]),
                 "gf2_mul_noalloc": (ctypes.c_int, [_P(Mat), _P(Mat), _P(Mat), _P(Opts), vp]),
+                "gf2_device_status": (ctypes.c_int, [vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -301,6 +302,11 @@ def gf2_describe_plan(m: int, l: int, n: int, options: Opts | None = None) -> st
 
 def gf2_strerror(status: int) -> str:
     return strerror(status)
+
+
+def gf2_device_status(stream=None) -> None:
+    """Raise GF2Error(GF2_ETIMEOUT) when a bounded device wait expired."""
+    _check(lib().gf2_device_status(_stream(stream)), "gf2_device_status")
 
 
 def gf2_profile_enable(on: bool) -> None:

@@ -502,6 +502,14 @@ int64_t gf2_launch_count(void) { return (int64_t)gf2::launch_count(); }
 
 int gf2_profile_enable(int32_t on) { return gf2::profile_enable(on); }
 
+int gf2_device_status(void *stream)
+{
+    unsigned int v = 0;
+    const int rc = gf2::tc_status_read_and_clear(&v, static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+    return v ? -(int)v : GF2_OK;
+}
+
 int gf2_profile_read(int32_t family, double *ms, int64_t *launches)
 {
     long long n = 0;

@@ -123,6 +123,7 @@ struct TcLaunch {
     unsigned int *status;                    // device word for timeouts (may be null)
 };
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
+int tc_status_read_and_clear(unsigned int *out, cudaStream_t s);
 bool tc_fp8_available();
 
 }  // namespace gf2

@@ -1,10 +1,466 @@
-// tc_fp8.cu -- tensor-core base case (placeholder until the tcgen05 kernel lands).
+// tc_fp8.cu -- exact tensor-core base case: C = A B over GF(2) from 0/1
+// FP8 products on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+// Why it is exact (Section 2.3): a GF(2) dot product is an AND followed by an
+// XOR accumulation, i.e. the parity of the INTEGER dot product of the 0/1
+// vectors.  Each bit is unpacked to the FP8 E4M3 value 2^-6 (byte 0x08) or 0,
+// so every product is 2^-12 or 0 and a dot product over a K-chunk of at most
+// KCHUNK = 4096 entries is count * 2^-12 with count <= 2^12: a multiple of
+// 2^-12 below 2 that any accumulator keeping 13 or more significant bits
+// holds exactly.  After each chunk the FP32 accumulator D is read from tensor
+// memory and the parity of count is the last mantissa bit of D + 2048 (whose
+// ulp is 2^-12); parities of successive chunks are XORed, which is the
+// GF(2) sum over the whole K range.
+//
+// Layout of one CTA (persistent, one per SM, 13 warps):
+//   warps 0-3  epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator (warp w
+//              reads TMEM lanes 32w..32w+31 = rows of the tile), parity,
+//              packed 64-bit words of C;
+//   warp 4     TMEM allocation (512 columns = two accumulators) and the MMA
+//              issuer (one thread): tcgen05.mma.cta_group::1.kind::f8f6f4,
+//              M = 128, N = 256, K = 32 per instruction;
+//   warps 5-12 producers: read the packed words of A (128 rows) and B^T (256
+//              rows) for a 128-entry K block, expand every bit to one FP8
+//              byte and store the tile in the 128-byte-swizzled K-major
+//              layout the MMA reads (4 stages of 48 KB in shared memory).
+// Hand-offs use mbarriers: full/empty per stage (producers <-> MMA, the MMA
+// side signalled by tcgen05.commit) and full/empty per accumulator
+// (MMA <-> epilogue).  Every wait is bounded; an expired wait records
+// GF2_ETIMEOUT in a device status word and the CTA winds down (waits for
+// its issued MMAs, frees its tensor memory) instead of hanging.
 #include "common.cuh"
 
+#include <mutex>
+
 namespace gf2 {
+namespace {
 
-bool tc_fp8_available() { return false; }
+constexpr int BM = 128;            // rows of A per tile (MMA M)
+constexpr int BN = 256;            // rows of B^T per tile (MMA N)
+constexpr int BK = 128;            // K entries per stage (128 FP8 bytes = one swizzle row)
+constexpr int STAGES = 4;
+constexpr int KCHUNK = 4096;       // exact-sum bound (entries per accumulation)
+constexpr int KB_PER_CHUNK = KCHUNK / BK;
+constexpr int A_BYTES = BM * BK;   // 16 KB
+constexpr int B_BYTES = BN * BK;   // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NUM_EPI_WARPS = 4;
+constexpr int MMA_WARP = 4;
+constexpr int NUM_PROD_WARPS = 8;
+constexpr int PROD_WARP0 = 5;
+constexpr int NTHREADS = (PROD_WARP0 + NUM_PROD_WARPS) * 32;   // 416
+constexpr int NPROD = NUM_PROD_WARPS * 32;                      // 256
+constexpr uint32_t TMEM_COLS = 512;
+constexpr unsigned long long WAIT_LIMIT = 4000000000ull;        // clock64 cycles (~2 s)
 
-int tc_fp8_launch(const TcLaunch &, cudaStream_t) { return GF2_EUNSUPPORTED; }
+// FP8 E4M3 0x08 = 2^-6: a 1-bit.  Instruction descriptor (kind::f8f6f4):
+// D format F32 (bits 4-5 = 1), A = B = E4M3 (bits 7-9, 10-12 = 0), both
+// K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+struct Params {
+    const uint64_t *A; int64_t lda, bsA;
+    const uint64_t *Bt; int64_t ldb, bsB;
+    uint64_t *C; int64_t ldc, bsC;
+    int64_t m, l, n;
+    int batch;
+    int tiles_m, tiles_n;
+    int64_t tiles;
+    int accumulate;
+    unsigned int *status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and the status word set) when the limit expires.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned int *status,
+                                          volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if ((unsigned long long)(clock64() - t0) > WAIT_LIMIT) {
+            if (status) atomicExch(status, (unsigned int)(-GF2_ETIMEOUT));
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast, so all
+// lanes leave together (the warp-collective tcgen05 instructions that
+// follow need every lane).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, unsigned int *status,
+                                          volatile int *abort_flag)
+{
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, status, abort_flag) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+// Warp-uniform read of the abort flag.
+__device__ __forceinline__ bool warp_aborted(volatile int *abort_flag)
+{
+    int a = 0;
+    if ((threadIdx.x & 31) == 0) a = *abort_flag;
+    return __shfl_sync(0xffffffffu, a, 0) != 0;
+}
+
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
+{
+    // tcgen05 shared-memory matrix descriptor: start >> 4, leading byte
+    // offset 16 (unused by swizzled K-major), stride byte offset 1024 (8
+    // rows x 128 bytes), fixed version 1 at bit 46, 128-byte swizzle (2).
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 4 bits -> 4 FP8 bytes (0x08 for a 1-bit): bit b lands on bit 8b + 3.
+__device__ __forceinline__ uint32_t spread4(uint32_t x4) { return (x4 * 0x01020408u) & 0x08080808u; }
+
+// Tile t -> (batch, tile row, tile column).
+__device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, int &tm, int &tn)
+{
+    const int64_t per = (int64_t)P.tiles_m * P.tiles_n;
+    b = (int)(t / per);
+    const int64_t r = t - (int64_t)b * per;
+    tm = (int)(r / P.tiles_n);
+    tn = (int)(r - (int64_t)tm * P.tiles_n);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // stage buffers must sit on 1024-byte boundaries (128-byte swizzle atoms)
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *sbase = smem_raw + (base - raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sbase + STAGES * STAGE_BYTES);
+    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t done_bar = bar0 + 8u * (2 * STAGES + 4);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), NPROD);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), NUM_EPI_WARPS * 32);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int64_t nkb = (P.l + BK - 1) / BK;            // K blocks per tile
+    const int nchunks = (int)((nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
+
+    if (warp >= PROD_WARP0) {
+        // ------------------------------------------------------------ producers
+        const int pt = threadIdx.x - PROD_WARP0 * 32;     // 0..255
+        uint32_t it = 0;                                   // stage use counter
+        for (int64_t t = blockIdx.x; t < P.tiles && !warp_aborted(abort_flag); t += gridDim.x) {
+            int b, tm, tn;
+            tile_coords(P, t, b, tm, tn);
+            const uint64_t *A = P.A + (int64_t)b * P.bsA;
+            const uint64_t *Bt = P.Bt + (int64_t)b * P.bsB;
+            const int64_t lW = words_of(P.l);
+            for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
+                const int s = (int)(it % STAGES);
+                const uint32_t ph = (it / STAGES) & 1u;
+                // load this thread's three half rows (64 entries each) first
+                uint64_t w[3];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int hr = pt + j * NPROD;             // 0..767: 256 half rows of A, 512 of B^T
+                    const int row = hr >> 1, half = hr & 1;
+                    const int64_t wi = kb * 2 + half;
+                    uint64_t v = 0;
+                    if (row < BM) {
+                        const int64_t gr = (int64_t)tm * BM + row;
+                        if (gr < P.m && wi < lW) v = __ldg(A + gr * P.lda + wi) & word_mask(wi, P.l);
+                    } else {
+                        const int64_t gr = (int64_t)tn * BN + (row - BM);
+                        if (gr < P.n && wi < lW) v = __ldg(Bt + gr * P.ldb + wi) & word_mask(wi, P.l);
+                    }
+                    w[j] = v;
+                }
+                if (!warp_wait(empty_bar(s), ph ^ 1u, P.status, abort_flag)) break;
+                unsigned char *st = sbase + s * STAGE_BYTES;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const int hr = pt + j * NPROD;
+                    const int row = hr >> 1, half = hr & 1;
+                    // row r of the A block, or row r-128 of the B block
+                    unsigned char *rowp = (row < BM) ? (st + (row >> 3) * 1024 + (row & 7) * 128)
+                                                     : (st + A_BYTES + ((row - BM) >> 3) * 1024 +
+                                                        ((row - BM) & 7) * 128);
+                    const int sw = row & 7;                    // (row - BM) & 7 == row & 7
+                    const uint32_t lo = (uint32_t)w[j], hi = (uint32_t)(w[j] >> 32);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {               // 16 entries -> one 16-byte chunk
+                        const uint32_t bits = (q < 2 ? lo : hi) >> ((q & 1) * 16);
+                        uint4 v;
+                        v.x = spread4(bits & 0xF);
+                        v.y = spread4((bits >> 4) & 0xF);
+                        v.z = spread4((bits >> 8) & 0xF);
+                        v.w = spread4((bits >> 12) & 0xF);
+                        const int chunk = (half * 4 + q) ^ sw;  // 128-byte swizzle
+                        *reinterpret_cast<uint4 *>(rowp + chunk * 16) = v;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(full_bar(s));
+            }
+        }
+    } else if (warp == MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, u = 0;                        // stage uses, accumulator units
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nchunks && ok; ++c, ++u) {
+                    const int ab = (int)(u & 1u);
+                    if (!mbar_wait(tempty_bar(ab), ((u >> 1) & 1u) ^ 1u, P.status, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t dt = tmem_base + (uint32_t)(ab * BN);
+                    const int64_t kb0 = (int64_t)c * KB_PER_CHUNK;
+                    const int64_t kb1 = min(nkb, kb0 + KB_PER_CHUNK);
+                    for (int64_t kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = (int)(it % STAGES);
+                        if (!mbar_wait(full_bar(s), (it / STAGES) & 1u, P.status, abort_flag)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sa = base + s * STAGE_BYTES;
+                        const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 32; ++kk) {
+                            // K step of 32 FP8 entries = 32 bytes inside the swizzle row
+                            mma_f8(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
+                                   (kb > kb0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit(empty_bar(s));          // stage free once these MMAs have read it
+                    }
+                    if (!ok) break;
+                    mma_commit(tfull_bar(ab));             // accumulator ready for the epilogue
+                }
+            }
+            // wind down: wait until every issued MMA has completed
+            mma_commit(done_bar);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(done_bar, 0)) {
+                if ((unsigned long long)(clock64() - t0) > WAIT_LIMIT) {
+                    if (P.status) atomicExch(P.status, (unsigned int)(-GF2_ETIMEOUT));
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int row_in_tile = warp * 32 + lane;          // TMEM lane = tile row
+        uint32_t u = 0;
+        for (int64_t t = blockIdx.x; t < P.tiles && !warp_aborted(abort_flag); t += gridDim.x) {
+            int b, tm, tn;
+            tile_coords(P, t, b, tm, tn);
+            uint32_t par[BN / 32];
+#pragma unroll
+            for (int i = 0; i < BN / 32; ++i) par[i] = 0;
+            bool ok = true;
+            for (int c = 0; c < nchunks; ++c, ++u) {
+                const int ab = (int)(u & 1u);
+                if (!warp_wait(tfull_bar(ab), (u >> 1) & 1u, P.status, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * BN);
+#pragma unroll 1
+                for (int g = 0; g < BN / 32; ++g) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + g * 32, r);
+                    tmem_wait_ld();
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        // D = count * 2^-12 < 2: the ulp of D + 2048 is 2^-12
+                        const uint32_t f = __float_as_uint(__uint_as_float(r[j]) + 2048.0f);
+                        word |= (f & 1u) << j;
+                    }
+                    par[g] ^= word;
+                }
+                tc_fence_before();
+                mbar_arrive(tempty_bar(ab));
+            }
+            if (!ok) break;
+            const int64_t grow = (int64_t)tm * BM + row_in_tile;
+            if (grow < P.m) {
+                uint64_t *C = P.C + (int64_t)b * P.bsC + grow * P.ldc;
+                const int64_t nW = words_of(P.n);
+#pragma unroll
+                for (int i = 0; i < BN / 64; ++i) {
+                    const int64_t wcol = (int64_t)tn * (BN / 64) + i;
+                    if (wcol < nW) {
+                        const uint64_t v = (((uint64_t)par[2 * i + 1] << 32) | par[2 * i]) & word_mask(wcol, P.n);
+                        C[wcol] = P.accumulate ? (C[wcol] ^ v) : v;
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+
+__device__ unsigned int g_tc_status;   // -GF2_ETIMEOUT after an expired wait
+
+}  // namespace
+
+bool tc_fp8_available()
+{
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return major == 10 && minor == 3;     // built for sm_103a only
+}
+
+int tc_status_read_and_clear(unsigned int *out, cudaStream_t s)
+{
+    unsigned int *p = nullptr;
+    GF2_CUDA_TRY(cudaGetSymbolAddress((void **)&p, g_tc_status));
+    unsigned int v = 0;
+    GF2_CUDA_TRY(cudaMemcpyAsync(&v, p, sizeof v, cudaMemcpyDeviceToHost, s));
+    GF2_CUDA_TRY(cudaStreamSynchronize(s));
+    GF2_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof v, s));
+    *out = v;
+    return GF2_OK;
+}
+
+int tc_fp8_launch(const TcLaunch &L, cudaStream_t s)
+{
+    if (L.batch <= 0 || L.m <= 0 || L.n <= 0) return GF2_OK;
+    Params P;
+    P.A = L.A; P.lda = L.lda; P.bsA = L.bsA;
+    P.Bt = L.Bt; P.ldb = L.ldb; P.bsB = L.bsB;
+    P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
+    P.m = L.m; P.l = L.l; P.n = L.n;
+    P.batch = L.batch;
+    P.tiles_m = div_up(L.m, BM);
+    P.tiles_n = div_up(L.n, BN);
+    P.tiles = (int64_t)L.batch * P.tiles_m * P.tiles_n;
+    P.accumulate = L.accumulate;
+    unsigned int *st = L.status;
+    if (!st) GF2_CUDA_TRY(cudaGetSymbolAddress((void **)&st, g_tc_status));
+    P.status = st;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(tc_fp8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return GF2_ECUDA;
+    int dev = 0, sms = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t grid = P.tiles < sms ? P.tiles : sms;
+    ProfScope ps(PF_TC, s);
+    tc_fp8_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(P);
+    note_launch();
+    return check_launch();
+}
 
 }  // namespace gf2
