@@ -12,14 +12,14 @@
 // ulp is 2^-12); parities of successive chunks are XORed, which is the
 // GF(2) sum over the whole K range.
 //
-// Layout of one CTA (persistent, one per SM, 13 warps):
+// Layout of one CTA (persistent, one per SM, 17 warps):
 //   warps 0-3  epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator (warp w
 //              reads TMEM lanes 32w..32w+31 = rows of the tile), parity,
 //              packed 64-bit words of C;
 //   warp 4     TMEM allocation (512 columns = two accumulators) and the MMA
 //              issuer (one thread): tcgen05.mma.cta_group::1.kind::f8f6f4,
 //              M = 128, N = 256, K = 32 per instruction;
-//   warps 5-12 producers: read the packed words of A (128 rows) and B^T (256
+//   warps 5-16 producers: read the packed words of A (128 rows) and B^T (256
 //              rows) for a 128-entry K block, expand every bit to one FP8
 //              byte and store the tile in the 128-byte-swizzled K-major
 //              layout the MMA reads (4 stages of 48 KB in shared memory).
@@ -46,10 +46,11 @@ constexpr int B_BYTES = BN * BK;   // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NUM_EPI_WARPS = 4;
 constexpr int MMA_WARP = 4;
-constexpr int NUM_PROD_WARPS = 8;
+constexpr int NUM_PROD_WARPS = 12;
 constexpr int PROD_WARP0 = 5;
-constexpr int NTHREADS = (PROD_WARP0 + NUM_PROD_WARPS) * 32;   // 416
-constexpr int NPROD = NUM_PROD_WARPS * 32;                      // 256
+constexpr int NTHREADS = (PROD_WARP0 + NUM_PROD_WARPS) * 32;   // 544
+constexpr int NPROD = NUM_PROD_WARPS * 32;                      // 384
+constexpr int PROD_ROWS = (2 * (BM + BN) + NPROD - 1) / NPROD;   // half rows per producer thread
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;        // clock64 cycles (~2 s)
 
@@ -244,60 +245,93 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
 
     if (warp >= PROD_WARP0) {
         // ------------------------------------------------------------ producers
-        const int pt = threadIdx.x - PROD_WARP0 * 32;     // 0..255
-        uint32_t it = 0;                                   // stage use counter
-        for (int64_t t = blockIdx.x; t < P.tiles && !warp_aborted(abort_flag); t += gridDim.x) {
+        // The CTA's stage uses form one sequence q = 0..Q-1 over (tile, K
+        // block); each thread keeps the packed words of the next PREF uses in
+        // registers so that global-load latency hides behind PREF stages.
+        const int pt = threadIdx.x - PROD_WARP0 * 32;     // 0..NPROD-1
+        const int64_t lW = words_of(P.l);
+        const int64_t my_tiles = (P.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        const int64_t Q = my_tiles * nkb;
+        // load cursor: the (tile, K block) of the next use to be loaded
+        int64_t cur_q = 0, cur_t = blockIdx.x, cur_kb = 0;
+        const uint64_t *cur_a = nullptr, *cur_b = nullptr;
+        int64_t cur_rowa = 0, cur_rowb = 0;
+        auto set_tile = [&]() {
             int b, tm, tn;
-            tile_coords(P, t, b, tm, tn);
-            const uint64_t *A = P.A + (int64_t)b * P.bsA;
-            const uint64_t *Bt = P.Bt + (int64_t)b * P.bsB;
-            const int64_t lW = words_of(P.l);
-            for (int64_t kb = 0; kb < nkb; ++kb, ++it) {
+            tile_coords(P, cur_t, b, tm, tn);
+            cur_a = P.A + (int64_t)b * P.bsA;
+            cur_b = P.Bt + (int64_t)b * P.bsB;
+            cur_rowa = (int64_t)tm * BM;
+            cur_rowb = (int64_t)tn * BN;
+        };
+        if (Q > 0) set_tile();
+        auto load_use = [&](uint64_t (&w)[PROD_ROWS]) {
+#pragma unroll
+            for (int j = 0; j < PROD_ROWS; ++j) w[j] = 0;
+            if (cur_q >= Q) return;
+#pragma unroll
+            for (int j = 0; j < PROD_ROWS; ++j) {
+                const int hr = pt + j * NPROD;             // half rows: 256 of A, 512 of B^T
+                if (hr >= 2 * (BM + BN)) continue;
+                const int row = hr >> 1, half = hr & 1;
+                const int64_t wi = cur_kb * 2 + half;
+                if (wi >= lW) continue;
+                if (row < BM) {
+                    const int64_t gr = cur_rowa + row;
+                    if (gr < P.m) w[j] = __ldg(cur_a + gr * P.lda + wi) & word_mask(wi, P.l);
+                } else {
+                    const int64_t gr = cur_rowb + (row - BM);
+                    if (gr < P.n) w[j] = __ldg(cur_b + gr * P.ldb + wi) & word_mask(wi, P.l);
+                }
+            }
+            ++cur_q;
+            if (++cur_kb == nkb) {
+                cur_kb = 0;
+                cur_t += gridDim.x;
+                if (cur_q < Q) set_tile();
+            }
+        };
+        constexpr int PREF = 4;
+        uint64_t pre[PREF][PROD_ROWS];
+#pragma unroll
+        for (int d = 0; d < PREF; ++d) load_use(pre[d]);
+        bool ok = true;
+        for (int64_t q0 = 0; q0 < Q && ok; q0 += PREF) {
+#pragma unroll
+            for (int d = 0; d < PREF; ++d) {
+                const int64_t q = q0 + d;
+                if (q >= Q) break;
+                const uint32_t it = (uint32_t)q;
                 const int s = (int)(it % STAGES);
                 const uint32_t ph = (it / STAGES) & 1u;
-                // load this thread's three half rows (64 entries each) first
-                uint64_t w[3];
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    const int hr = pt + j * NPROD;             // 0..767: 256 half rows of A, 512 of B^T
-                    const int row = hr >> 1, half = hr & 1;
-                    const int64_t wi = kb * 2 + half;
-                    uint64_t v = 0;
-                    if (row < BM) {
-                        const int64_t gr = (int64_t)tm * BM + row;
-                        if (gr < P.m && wi < lW) v = __ldg(A + gr * P.lda + wi) & word_mask(wi, P.l);
-                    } else {
-                        const int64_t gr = (int64_t)tn * BN + (row - BM);
-                        if (gr < P.n && wi < lW) v = __ldg(Bt + gr * P.ldb + wi) & word_mask(wi, P.l);
-                    }
-                    w[j] = v;
-                }
-                if (!warp_wait(empty_bar(s), ph ^ 1u, P.status, abort_flag)) break;
+                if (!warp_wait(empty_bar(s), ph ^ 1u, P.status, abort_flag)) { ok = false; break; }
                 unsigned char *st = sbase + s * STAGE_BYTES;
 #pragma unroll
-                for (int j = 0; j < 3; ++j) {
+                for (int j = 0; j < PROD_ROWS; ++j) {
                     const int hr = pt + j * NPROD;
+                    if (hr >= 2 * (BM + BN)) continue;
                     const int row = hr >> 1, half = hr & 1;
                     // row r of the A block, or row r-128 of the B block
                     unsigned char *rowp = (row < BM) ? (st + (row >> 3) * 1024 + (row & 7) * 128)
                                                      : (st + A_BYTES + ((row - BM) >> 3) * 1024 +
                                                         ((row - BM) & 7) * 128);
                     const int sw = row & 7;                    // (row - BM) & 7 == row & 7
-                    const uint32_t lo = (uint32_t)w[j], hi = (uint32_t)(w[j] >> 32);
+                    const uint32_t lo = (uint32_t)pre[d][j], hi = (uint32_t)(pre[d][j] >> 32);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {               // 16 entries -> one 16-byte chunk
-                        const uint32_t bits = (q < 2 ? lo : hi) >> ((q & 1) * 16);
+                    for (int qq = 0; qq < 4; ++qq) {            // 16 entries -> one 16-byte chunk
+                        const uint32_t bits = (qq < 2 ? lo : hi) >> ((qq & 1) * 16);
                         uint4 v;
                         v.x = spread4(bits & 0xF);
                         v.y = spread4((bits >> 4) & 0xF);
                         v.z = spread4((bits >> 8) & 0xF);
                         v.w = spread4((bits >> 12) & 0xF);
-                        const int chunk = (half * 4 + q) ^ sw;  // 128-byte swizzle
+                        const int chunk = (half * 4 + qq) ^ sw; // 128-byte swizzle
                         *reinterpret_cast<uint4 *>(rowp + chunk * 16) = v;
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(full_bar(s));
+                load_use(pre[d]);
             }
         }
     } else if (warp == MMA_WARP) {
