@@ -118,6 +118,33 @@ int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[],
                     const gf2_mat *const B[], int32_t count,
                     const gf2_opts *opts, void *cuda_stream);
 
+/* gf2_mul_batched_ex: gf2_mul_batched with the batched base case's tile
+ * variant pinned (variant >= 0, see gf2_batched_variant_name) or chosen by
+ * the autotuner (variant = -1).  *chosen (may be NULL) receives the variant
+ * used.  Details of the batched form:
+ *  - products whose automatic plan recurses (every dimension >= 8192) or that
+ *    request depth > 0 or the tensor-core base are run one by one as gf2_mul;
+ *    all others go into ONE persistent launch of the packed M4RM kernel
+ *    whose CTAs pull tiles of all products from one work queue, longest K
+ *    first;
+ *  - the first call for a set of operands (pointers, shapes, strides,
+ *    stream, options) times every variant on that batch (the autotuner),
+ *    keeps the fastest, and builds a CUDA graph {reset the queue, launch};
+ *    later calls with the same operands replay the graph.  The tuned choice
+ *    is cached per shape signature and, when the environment variable
+ *    GF2_TUNE_CACHE names a file, persisted there as JSON;
+ *  - the first call synchronises the stream (autotuning, table upload).
+ */
+int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[],
+                       const gf2_mat *const B[], int32_t count,
+                       const gf2_opts *opts, int32_t variant, int32_t *chosen,
+                       void *cuda_stream);
+
+/* Number of tile variants of the batched base case, and the name of one
+ * ("k<k>t<t>-w<columns>-bm<rows>"; NULL beyond the last). */
+int32_t gf2_batched_variant_count(void);
+const char *gf2_batched_variant_name(int32_t variant);
+
 /* ---- steps of the path, callable alone ------------------------------------
  * gf2_sw_split: the 8 additions of Algorithm 4 for one level.  From X
  * (rows x cols, both even, cols a multiple of 128) writes the 7 operands of

@@ -51,7 +51,8 @@ EXPORTS = (
     "gf2_sw_split", "gf2_sw_combine", "gf2_make_table", "gf2_random", "gf2_transpose",
     "gf2_freivalds", "gf2_scratch_bytes", "gf2_reserve_scratch", "gf2_release_scratch",
     "gf2_launch_count", "gf2_describe_plan", "gf2_profile_enable", "gf2_profile_read",
-    "gf2_profile_name", "gf2_mul_noalloc", "gf2_device_status",
+    "gf2_profile_name", "gf2_mul_noalloc", "gf2_device_status", "gf2_mul_batched_ex",
+    "gf2_batched_variant_count", "gf2_batched_variant_name",
 )
 
 
@@ -135,6 +136,10 @@ def lib():
                 "gf2_profile_name": (ctypes.c_char_p, [i32]),
                 "gf2_mul_noalloc": (ctypes.c_int, [_P(Mat), _P(Mat), _P(Mat), _P(Opts), vp]),
                 "gf2_device_status": (ctypes.c_int, [vp]),
+                "gf2_mul_batched_ex": (ctypes.c_int, [_P(_P(Mat)), _P(_P(Mat)), _P(_P(Mat)), i32,
+                                                      _P(Opts), i32, _P(i32), vp]),
+                "gf2_batched_variant_count": (i32, []),
+                "gf2_batched_variant_name": (ctypes.c_char_p, [i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -226,19 +231,50 @@ def gf2_mul_noalloc(C: Mat, A: Mat, B: Mat, options: Opts | None = None, stream=
                                  _stream(stream)), "gf2_mul_noalloc")
 
 
-def gf2_mul_batched(C: list, A: list, B: list, options: Opts | None = None, stream=None) -> None:
-    n = len(A)
-    if len(B) != n or len(C) != n:
-        raise ValueError("C, A, B need the same length")
-    arrs = []
-    for seq in (C, A, B):
-        arr = (_P(Mat) * max(n, 1))()
-        for i, M in enumerate(seq):
-            arr[i] = ctypes.pointer(M)
-        arrs.append(arr)
+class MatArrays:
+    """Pointer arrays for the batched calls (build once, reuse: the batched
+    form caches its plan and CUDA graph per set of operands)."""
+
+    def __init__(self, C: list, A: list, B: list):
+        n = len(A)
+        if len(B) != n or len(C) != n:
+            raise ValueError("C, A, B need the same length")
+        self.n = n
+        self.keep = (list(C), list(A), list(B))
+        self.arrs = []
+        for seq in self.keep:
+            arr = (_P(Mat) * max(n, 1))()
+            for i, M in enumerate(seq):
+                arr[i] = ctypes.pointer(M)
+            self.arrs.append(arr)
+
+
+def gf2_mul_batched(C, A=None, B=None, options: Opts | None = None, stream=None) -> None:
+    """C[i] = A[i] B[i]; pass three lists, or one MatArrays."""
+    arrs = C if isinstance(C, MatArrays) else MatArrays(C, A, B)
     o = ctypes.byref(options) if options is not None else None
-    _check(lib().gf2_mul_batched(arrs[0], arrs[1], arrs[2], n, o, _stream(stream)),
+    _check(lib().gf2_mul_batched(arrs.arrs[0], arrs.arrs[1], arrs.arrs[2], arrs.n, o, _stream(stream)),
            "gf2_mul_batched")
+
+
+def gf2_mul_batched_ex(C, A=None, B=None, options: Opts | None = None, variant: int = -1,
+                       stream=None) -> int:
+    """gf2_mul_batched with a pinned tile variant (or -1: autotuned); returns the variant used."""
+    arrs = C if isinstance(C, MatArrays) else MatArrays(C, A, B)
+    o = ctypes.byref(options) if options is not None else None
+    ch = ctypes.c_int32(-1)
+    _check(lib().gf2_mul_batched_ex(arrs.arrs[0], arrs.arrs[1], arrs.arrs[2], arrs.n, o, variant,
+                                    ctypes.byref(ch), _stream(stream)), "gf2_mul_batched_ex")
+    return ch.value
+
+
+def gf2_batched_variant_count() -> int:
+    return int(lib().gf2_batched_variant_count())
+
+
+def gf2_batched_variant_name(i: int):
+    r = lib().gf2_batched_variant_name(i)
+    return r.decode() if r else None
 
 
 def gf2_sw_split(out_ptr: int, slab_words: int, X: Mat, side: int, stream=None) -> None:

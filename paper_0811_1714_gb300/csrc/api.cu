@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <utility>
+#include <vector>
 
 namespace gf2 {
 long long launch_count();
@@ -485,6 +486,7 @@ int gf2_release_scratch(void)
 {
     int dev = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));
+    gf2::batched_release();
     std::lock_guard<std::mutex> lk(g_arena_mu);
     GF2_CUDA_TRY(cudaDeviceSynchronize());
     for (auto it = g_arenas.begin(); it != g_arenas.end();) {
@@ -588,14 +590,17 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
     return GF2_OK;
 }
 
-int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[],
-                    int32_t count, const gf2_opts *opts, void *stream)
+int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[],
+                       int32_t count, const gf2_opts *opts, int32_t variant, int32_t *chosen, void *stream)
 {
     if (count < 0 || (count > 0 && (!C || !A || !B))) return GF2_EINVAL;
     const gf2_opts o = resolve(opts);
     int rc = check_opts(o);
     if (rc) return rc;
+    if (variant < -1 || variant >= gf2::batched_variant_count()) return GF2_EINVAL;
+    int dev = 0;
     for (int i = 0; i < count; ++i) {
+        if (!C[i] || !A[i] || !B[i]) return GF2_EINVAL;
         if ((rc = check_mat(A[i])) || (rc = check_mat(B[i])) || (rc = check_mat(C[i]))) return rc;
         if (A[i]->cols != B[i]->rows || C[i]->rows != A[i]->rows || C[i]->cols != B[i]->cols)
             return GF2_EINVAL;
@@ -603,12 +608,48 @@ int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat 
             return GF2_EINVAL;
         if (overlaps(C[i], A[i]) || overlaps(C[i], B[i])) return GF2_EALIAS;
     }
+    if (chosen) *chosen = -1;
+    if (count == 0) return GF2_OK;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
     for (int i = 0; i < count; ++i) {
-        rc = gf2_mul(C[i], A[i], B[i], &o, stream);
-        if (rc) return rc;
+        const gf2_mat *ms[3] = {A[i], B[i], C[i]};
+        for (const gf2_mat *M : ms)
+            if (M->rows && M->cols && M->device != dev) return GF2_EINVAL;
     }
-    return GF2_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // products for the single persistent launch, and the rest (recursing or
+    // tensor-core plans) run one by one
+    std::vector<gf2_mat *> bc;
+    std::vector<const gf2_mat *> ba, bb;
+    for (int i = 0; i < count; ++i) {
+        const int64_t m = A[i]->rows, l = A[i]->cols, n = B[i]->cols;
+        const int base = o.base == GF2_BASE_AUTO ? GF2_BASE_M4RM : o.base;
+        const int depth = o.depth < 0 ? auto_depth(m, l, n, base) : o.depth;
+        if (base == GF2_BASE_M4RM && depth == 0) {
+            bc.push_back(C[i]);
+            ba.push_back(A[i]);
+            bb.push_back(B[i]);
+        } else {
+            rc = gf2_mul(C[i], A[i], B[i], &o, stream);
+            if (rc) return rc;
+        }
+    }
+    if (bc.empty()) return GF2_OK;
+    int ch = -1;
+    rc = gf2::batched_mul(bc.data(), ba.data(), bb.data(), (int)bc.size(), o.accumulate, variant, s, &ch);
+    if (chosen) *chosen = ch;
+    return rc;
 }
+
+int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[],
+                    int32_t count, const gf2_opts *opts, void *stream)
+{
+    return gf2_mul_batched_ex(C, A, B, count, opts, -1, nullptr, stream);
+}
+
+int32_t gf2_batched_variant_count(void) { return gf2::batched_variant_count(); }
+
+const char *gf2_batched_variant_name(int32_t variant) { return gf2::batched_variant_name(variant); }
 
 int gf2_sw_split(uint64_t *out, int64_t slab_words, const gf2_mat *X, int32_t side, void *stream)
 {

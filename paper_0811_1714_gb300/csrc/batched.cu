@@ -1,0 +1,543 @@
+// batched.cu -- many independent products of uneven shapes in ONE persistent
+// launch, replayed as a CUDA graph, with the tile shape chosen by an
+// autotuner (the batched form of the Method of the Four Russians base case,
+// Section 3, Algorithms 1-3).
+//
+// Device side: a persistent kernel whose CTAs pull tiles from one atomic
+// work counter.  A tile is (product, first row, first word) of a C block of
+// BM rows x LPR*128 columns; every product has its own A, B, C pointers,
+// strides and sizes in a descriptor table.  Tiles are ordered by decreasing
+// K extent (longest first) so the queue drains evenly.
+//
+// Host side (gf2_mul_batched): the first call for a set of operands builds
+// the descriptor tables, lets the autotuner time every candidate variant on
+// that batch (candidates differ in k, t, tile rows BM and tile width), keeps
+// the fastest, and builds a CUDA graph {reset counter, persistent kernel}.
+// Later calls with the same operands replay the graph.  The autotuner's
+// choices are cached per shape signature, and can be persisted to the JSON
+// file named by the GF2_TUNE_CACHE environment variable.
+#include "common.cuh"
+#include "m4rm_dev.cuh"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+namespace gf2 {
+namespace {
+
+using namespace m4rm_dev;
+
+struct BProd {
+    const uint64_t *A;
+    const uint64_t *B;
+    uint64_t *C;
+    int64_t lda, ldb, ldc;
+    int64_t m, l, n;
+};
+
+struct BTile {
+    int prod;
+    int row0;
+    int word0;
+    int pad;
+};
+
+template <int KB, int NT, int LPR, int R, int NW>
+__global__ void __launch_bounds__(NW * 32) m4rm_batched_kernel(const BProd *__restrict__ prods,
+                                                               const BTile *__restrict__ tiles, int ntiles,
+                                                               unsigned int *counter, int accumulate)
+{
+    constexpr int NTH = NW * 32;
+    constexpr int KG = KB * NT;
+    constexpr int TROWS = 1 << KB;
+    constexpr int RPS = 32 / LPR;                 // rows per warp step
+    constexpr int BM = NW * RPS * R;
+    constexpr int TW = 2 * LPR;                   // words per tile row
+    constexpr unsigned IMASK = (1u << KB) - 1u;
+    static_assert(KG <= 64, "");
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);   // NT * TROWS * LPR
+    uint4 *stg = tab + NT * TROWS * LPR;                  // 2 * KG * LPR
+    uint4 *sta = stg + 2 * KG * LPR;                      // 2 * BM
+    __shared__ int s_tile;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int chunk = lane % LPR;
+    const int trow = warp * RPS * R + lane / LPR;         // tile row of row-group r: trow + RPS*r
+
+    while (true) {
+        if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        const BTile T = tiles[t];
+        const BProd P = prods[T.prod];
+        const int64_t row0 = T.row0;
+        const int64_t w0 = T.word0;
+        const int64_t nW = words_of(P.n);
+        const int64_t lW = words_of(P.l);
+        const int groups = (int)((P.l + KG - 1) / KG);
+        const int64_t cw = w0 + 2 * chunk;
+        const uint64_t cm0 = word_mask(cw, P.n), cm1 = word_mask(cw + 1, P.n);
+        const uint4 cmask = make_uint4((uint32_t)cm0, (uint32_t)(cm0 >> 32), (uint32_t)cm1,
+                                       (uint32_t)(cm1 >> 32));
+        uint4 acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+
+        auto issue_stage = [&](int g, int buf) {
+#pragma unroll 1
+            for (int i = tid; i < KG * LPR; i += NTH) {
+                const int rr = i / LPR, cc = i % LPR;
+                const int64_t brow = (int64_t)g * KG + rr;
+                const int64_t bw = w0 + 2 * cc;
+                const bool valid = (brow < P.l) && (bw < nW);
+                cp_async16(&stg[buf * KG * LPR + i], valid ? (P.B + brow * P.ldb + bw) : P.B, valid);
+            }
+            const int64_t kb = (int64_t)g * KG;
+            const int64_t wa = kb >> 6;
+            const bool two = ((kb & 63) + KG > 64) && (wa + 1 < lW);
+#pragma unroll 1
+            for (int i = tid; i < BM; i += NTH) {
+                const int64_t row = row0 + i;
+                const bool valid = row < P.m;
+                const uint64_t *src = P.A + (valid ? row * P.lda + wa : 0);
+                uint4 *dst = &sta[buf * BM + i];
+                cp_async8(dst, src, valid);
+                if (two) cp_async8(reinterpret_cast<char *>(dst) + 8, src + 1, valid);
+            }
+            cp_async_commit();
+        };
+
+        if (groups > 0) issue_stage(0, 0);
+#pragma unroll 1
+        for (int g = 0; g < groups; ++g) {
+            const int buf = g & 1;
+            cp_async_wait_all();
+            __syncthreads();
+            if (g + 1 < groups) issue_stage(g + 1, buf ^ 1);
+            build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
+            __syncthreads();
+            const int64_t kb = (int64_t)g * KG;
+            const int64_t wa = kb >> 6;
+            const int sh = (int)(kb & 63);
+            const uint64_t mlo = word_mask(wa, P.l);
+            const uint64_t mhi = (sh + KG > 64) ? word_mask(wa + 1, P.l) : 0ull;
+            const uint4 *arow = sta + buf * BM + trow;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint2 aw = *reinterpret_cast<const uint2 *>(&arow[RPS * r]);
+                uint64_t bits = (((uint64_t)aw.y << 32 | aw.x) & mlo) >> sh;
+                if (sh + KG > 64) {
+                    const uint2 aw2 = reinterpret_cast<const uint2 *>(&arow[RPS * r])[1];
+                    bits |= (((uint64_t)aw2.y << 32 | aw2.x) & mhi) << (64 - sh);
+                }
+                uint4 a = acc[r];
+#pragma unroll
+                for (int ti = 0; ti < NT; ++ti) {
+                    const unsigned x = (unsigned)(bits >> (ti * KB)) & IMASK;
+                    a = x4(a, tab[(ti * TROWS + (int)x) * LPR + chunk]);
+                }
+                acc[r] = a;
+                asm volatile("" ::: "memory");
+            }
+        }
+
+        if (cw < nW) {
+            const int64_t first = row0 + trow;
+            const int64_t left = P.m - first;
+            const int nrows = left <= 0 ? 0 : (left < RPS * R ? (int)left : RPS * R);
+            uint64_t *cr = P.C + first * P.ldc + cw;
+            const int64_t step = (int64_t)RPS * P.ldc;
+            if (!accumulate && cw + 1 < nW) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (RPS * r < nrows) *reinterpret_cast<uint4 *>(cr + r * step) = and4(acc[r], cmask);
+            } else {
+                const bool two = (cw + 1 < nW);
+#pragma unroll 1
+                for (int r = 0; r < R; ++r) {
+                    if (RPS * r >= nrows) break;
+                    uint4 a = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+                        if (q == r) a = acc[q];
+                    const uint64_t v0 = ((uint64_t)a.y << 32 | a.x) & cm0;
+                    const uint64_t v1 = ((uint64_t)a.w << 32 | a.z) & cm1;
+                    uint64_t *c = cr + r * step;
+                    if (accumulate) {
+                        c[0] ^= v0;
+                        if (two) c[1] ^= v1;
+                    } else {
+                        c[0] = v0;
+                    }
+                }
+            }
+        }
+        (void)TW;
+        __syncthreads();    // s_tile and shared buffers are reused by the next tile
+    }
+}
+
+using BatchedFn = void (*)(const BProd *, const BTile *, int, unsigned int *, int);
+
+struct BVariant {
+    const char *name;
+    int k, t, lpr, bm, nw;
+    BatchedFn fn;
+    int smem;
+};
+
+template <int KB, int NT, int LPR, int R, int NW>
+BVariant make_bvariant(const char *name)
+{
+    constexpr int BM = NW * (32 / LPR) * R;
+    return BVariant{name, KB, NT, LPR, BM, NW, &m4rm_batched_kernel<KB, NT, LPR, R, NW>,
+                    NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16};
+}
+
+const std::vector<BVariant> &bvariants()
+{
+    static const std::vector<BVariant> v = {
+        make_bvariant<8, 4, 8, 32, 8>("k8t4-w1024-bm1024"),
+        make_bvariant<6, 8, 8, 8, 8>("k6t8-w1024-bm256"),
+        make_bvariant<6, 8, 4, 8, 8>("k6t8-w512-bm512"),
+        make_bvariant<5, 8, 4, 4, 8>("k5t8-w512-bm256"),
+        make_bvariant<4, 8, 4, 4, 8>("k4t8-w512-bm256"),
+        make_bvariant<6, 8, 2, 4, 8>("k6t8-w256-bm512"),
+        make_bvariant<4, 8, 2, 2, 8>("k4t8-w256-bm256"),
+        make_bvariant<8, 4, 4, 16, 8>("k8t4-w512-bm1024"),
+    };
+    return v;
+}
+
+// ------------------------------------------------------------------ planning
+
+struct Built {
+    int variant = -1;
+    std::vector<BProd> prods;
+    std::vector<BTile> tiles;
+};
+
+void build_tiles(const std::vector<BProd> &prods, const BVariant &v, std::vector<BTile> &tiles)
+{
+    tiles.clear();
+    const int tw = 2 * v.lpr;
+    for (size_t i = 0; i < prods.size(); ++i) {
+        const BProd &p = prods[i];
+        if (p.m <= 0 || p.n <= 0) continue;
+        const int64_t W = words_of(p.n);
+        for (int64_t r = 0; r < p.m; r += v.bm)
+            for (int64_t w = 0; w < W; w += tw) tiles.push_back(BTile{(int)i, (int)r, (int)w, 0});
+    }
+    // longest K first (the work of a tile grows with the K extent)
+    std::stable_sort(tiles.begin(), tiles.end(), [&](const BTile &a, const BTile &b) {
+        return prods[a.prod].l > prods[b.prod].l;
+    });
+}
+
+int grid_for(const BVariant &v)
+{
+    int dev = 0, sms = 1, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, v.fn, v.nw * 32, v.smem) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    return sms * per;
+}
+
+// Shape signature used by the autotuner's cache: the sorted list of shapes.
+std::string signature(const std::vector<BProd> &prods, int accumulate)
+{
+    std::vector<unsigned long long> key;
+    key.reserve(prods.size());
+    for (const BProd &p : prods)
+        key.push_back(((unsigned long long)p.m << 42) ^ ((unsigned long long)p.l << 21) ^ (unsigned long long)p.n);
+    std::sort(key.begin(), key.end());
+    unsigned long long h = 1469598103934665603ull;
+    for (unsigned long long k : key) {
+        h ^= k;
+        h *= 1099511628211ull;
+    }
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    char buf[96];
+    snprintf(buf, sizeof buf, "sm%d%d-n%zu-a%d-%016llx", major, minor, prods.size(), accumulate, h);
+    return buf;
+}
+
+// ------------------------------------------------------------------ tune cache
+std::mutex g_mu;
+std::map<std::string, std::string> g_tuned;   // signature -> variant name
+bool g_tuned_loaded = false;
+
+void load_tune_cache()
+{
+    if (g_tuned_loaded) return;
+    g_tuned_loaded = true;
+    const char *path = getenv("GF2_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    // one entry per line: "signature": "variant",
+    while (fgets(line, sizeof line, f)) {
+        char k[256], v[128];
+        if (sscanf(line, " \"%255[^\"]\" : \"%127[^\"]\"", k, v) == 2) g_tuned[k] = v;
+    }
+    fclose(f);
+}
+
+void save_tune_cache()
+{
+    const char *path = getenv("GF2_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto &kv : g_tuned)
+        fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kv.second.c_str(), ++i < g_tuned.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
+
+// ------------------------------------------------------------------ graphs
+struct GraphEntry {
+    std::vector<unsigned long long> key;    // operand pointers, sizes, strides, stream, options
+    int variant = -1;
+    void *dev = nullptr;                     // descriptor tables + counter (one cudaMalloc)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int ntiles = 0;
+};
+std::list<GraphEntry> g_graphs;             // most recently used first
+constexpr size_t kMaxGraphs = 8;
+
+void free_entry(GraphEntry &e)
+{
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    if (e.dev) cudaFree(e.dev);
+    e.exec = nullptr;
+    e.graph = nullptr;
+    e.dev = nullptr;
+}
+
+// Device copies of the tables: [prods][tiles][counter]
+int upload(const std::vector<BProd> &prods, const std::vector<BTile> &tiles, void **dev, BProd **dp,
+           BTile **dt, unsigned int **dc)
+{
+    const size_t bp = (prods.size() * sizeof(BProd) + 255) & ~(size_t)255;
+    const size_t bt = (tiles.size() * sizeof(BTile) + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (cudaMalloc(&p, bp + bt + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return GF2_ENOMEM;
+    }
+    char *c = static_cast<char *>(p);
+    GF2_CUDA_TRY(cudaMemcpy(c, prods.data(), prods.size() * sizeof(BProd), cudaMemcpyHostToDevice));
+    if (!tiles.empty())
+        GF2_CUDA_TRY(cudaMemcpy(c + bp, tiles.data(), tiles.size() * sizeof(BTile), cudaMemcpyHostToDevice));
+    *dev = p;
+    *dp = reinterpret_cast<BProd *>(c);
+    *dt = reinterpret_cast<BTile *>(c + bp);
+    *dc = reinterpret_cast<unsigned int *>(c + bp + bt);
+    return GF2_OK;
+}
+
+int launch_variant(const BVariant &v, const BProd *dp, const BTile *dt, int ntiles, unsigned int *dc,
+                   int accumulate, cudaStream_t s)
+{
+    GF2_CUDA_TRY(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
+    GF2_CUDA_TRY(cudaMemsetAsync(dc, 0, sizeof(unsigned int), s));
+    ProfScope ps(PF_BATCHED, s);
+    v.fn<<<grid_for(v), v.nw * 32, v.smem, s>>>(dp, dt, ntiles, dc, accumulate);
+    note_launch();
+    return check_launch();
+}
+
+// Times every candidate on this batch (two runs each after one warm-up) and
+// returns the index of the fastest.
+int autotune(const std::vector<BProd> &prods, int accumulate, cudaStream_t s)
+{
+    const auto &vs = bvariants();
+    int best = 0;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    GF2_CUDA_TRY(cudaEventCreate(&e0));
+    GF2_CUDA_TRY(cudaEventCreate(&e1));
+    for (size_t i = 0; i < vs.size(); ++i) {
+        std::vector<BTile> tiles;
+        build_tiles(prods, vs[i], tiles);
+        void *dev = nullptr;
+        BProd *dp;
+        BTile *dt;
+        unsigned int *dc;
+        if (upload(prods, tiles, &dev, &dp, &dt, &dc)) continue;
+        float ms = 1e30f;
+        bool ok = launch_variant(vs[i], dp, dt, (int)tiles.size(), dc, accumulate, s) == GF2_OK;
+        for (int rep = 0; ok && rep < 2; ++rep) {
+            cudaEventRecord(e0, s);
+            ok = launch_variant(vs[i], dp, dt, (int)tiles.size(), dc, accumulate, s) == GF2_OK;
+            cudaEventRecord(e1, s);
+            float t = 0.f;
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+                ms = std::min(ms, t);
+        }
+        cudaStreamSynchronize(s);
+        cudaFree(dev);
+        cudaGetLastError();
+        if (ok && ms < best_ms) {
+            best_ms = ms;
+            best = (int)i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+}  // namespace
+
+int batched_variant_count() { return (int)bvariants().size(); }
+
+const char *batched_variant_name(int i)
+{
+    const auto &vs = bvariants();
+    return (i >= 0 && i < (int)vs.size()) ? vs[i].name : nullptr;
+}
+
+// C[i] = A[i] B[i] for device operands (arguments already checked).
+// `force_variant` >= 0 skips the autotuner.
+int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[], int count,
+                int accumulate, int force_variant, cudaStream_t s, int *chosen)
+{
+    std::vector<BProd> prods;
+    prods.reserve(count);
+    std::vector<unsigned long long> key;
+    key.reserve(6 * (size_t)count + 4);
+    for (int i = 0; i < count; ++i) {
+        BProd p;
+        p.A = A[i]->data; p.B = B[i]->data; p.C = C[i]->data;
+        p.lda = A[i]->stride_words; p.ldb = B[i]->stride_words; p.ldc = C[i]->stride_words;
+        p.m = A[i]->rows; p.l = A[i]->cols; p.n = B[i]->cols;
+        prods.push_back(p);
+        key.push_back((unsigned long long)(uintptr_t)p.A);
+        key.push_back((unsigned long long)(uintptr_t)p.B);
+        key.push_back((unsigned long long)(uintptr_t)p.C);
+        key.push_back(((unsigned long long)p.lda << 32) ^ (unsigned long long)p.ldb ^ ((unsigned long long)p.ldc << 16));
+        key.push_back(((unsigned long long)p.m << 40) ^ ((unsigned long long)p.l << 20) ^ (unsigned long long)p.n);
+    }
+    int dev = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    key.push_back((unsigned long long)(uintptr_t)s);
+    key.push_back((unsigned long long)dev);
+    key.push_back((unsigned long long)accumulate);
+    key.push_back((unsigned long long)(force_variant + 1));
+
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end(); ++it) {
+        if (it->key == key) {
+            g_graphs.splice(g_graphs.begin(), g_graphs, it);       // most recently used
+            if (chosen) *chosen = g_graphs.front().variant;
+            if (g_graphs.front().ntiles == 0) return GF2_OK;
+            GF2_CUDA_TRY(cudaGraphLaunch(g_graphs.front().exec, s));
+            note_launch();
+            return GF2_OK;
+        }
+    }
+
+    // choose the variant: forced, cached for this shape signature, or tuned now
+    const auto &vs = bvariants();
+    int vi = force_variant;
+    if (vi < 0 || vi >= (int)vs.size()) {
+        load_tune_cache();
+        const std::string sig = signature(prods, accumulate);
+        auto f = g_tuned.find(sig);
+        vi = -1;
+        if (f != g_tuned.end())
+            for (size_t i = 0; i < vs.size(); ++i)
+                if (f->second == vs[i].name) vi = (int)i;
+        if (vi < 0) {
+            vi = autotune(prods, accumulate, s);
+            g_tuned[sig] = vs[vi].name;
+            save_tune_cache();
+        }
+    }
+    const BVariant &v = vs[vi];
+
+    GraphEntry e;
+    e.key = key;
+    e.variant = vi;
+    std::vector<BTile> tiles;
+    build_tiles(prods, v, tiles);
+    e.ntiles = (int)tiles.size();
+    if (e.ntiles > 0) {
+        BProd *dp;
+        BTile *dt;
+        unsigned int *dc;
+        int rc = upload(prods, tiles, &e.dev, &dp, &dt, &dc);
+        if (rc) return rc;
+        GF2_CUDA_TRY(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
+        // graph: reset the work counter, then the persistent kernel
+        if (cudaGraphCreate(&e.graph, 0) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        cudaGraphNode_t nmem, nker;
+        cudaMemsetParams mp;
+        memset(&mp, 0, sizeof mp);
+        mp.dst = dc;
+        mp.value = 0;
+        mp.elementSize = sizeof(unsigned int);
+        mp.width = 1;
+        mp.height = 1;
+        mp.pitch = sizeof(unsigned int);
+        if (cudaGraphAddMemsetNode(&nmem, e.graph, nullptr, 0, &mp) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        int nt = e.ntiles;
+        void *args[5] = {(void *)&dp, (void *)&dt, (void *)&nt, (void *)&dc, (void *)&accumulate};
+        cudaKernelNodeParams kp;
+        memset(&kp, 0, sizeof kp);
+        kp.func = (void *)v.fn;
+        kp.gridDim = dim3((unsigned)grid_for(v));
+        kp.blockDim = dim3((unsigned)(v.nw * 32));
+        kp.sharedMemBytes = (unsigned)v.smem;
+        kp.kernelParams = args;
+        if (cudaGraphAddKernelNode(&nker, e.graph, &nmem, 1, &kp) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        if (cudaGraphInstantiate(&e.exec, e.graph, 0) != cudaSuccess) { free_entry(e); cudaGetLastError(); return GF2_ECUDA; }
+        if (cudaGraphLaunch(e.exec, s) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        note_launch();
+    }
+    g_graphs.push_front(std::move(e));
+    while (g_graphs.size() > kMaxGraphs) {
+        // an older graph may still be running on its stream: wait before freeing
+        cudaDeviceSynchronize();
+        free_entry(g_graphs.back());
+        g_graphs.pop_back();
+    }
+    if (chosen) *chosen = vi;
+    return GF2_OK;
+}
+
+void batched_release()
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_graphs.empty()) cudaDeviceSynchronize();
+    for (GraphEntry &e : g_graphs) free_entry(e);
+    g_graphs.clear();
+}
+
+}  // namespace gf2

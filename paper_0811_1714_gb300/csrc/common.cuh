@@ -123,6 +123,13 @@ struct TcLaunch {
     unsigned int *status;                    // device word for timeouts (may be null)
 };
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
+
+// Batched persistent M4RM (one launch, graph-replayed, autotuned).
+int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[], int count,
+                int accumulate, int force_variant, cudaStream_t s, int *chosen);
+int batched_variant_count();
+const char *batched_variant_name(int i);
+void batched_release();
 int tc_status_read_and_clear(unsigned int *out, cudaStream_t s);
 bool tc_fp8_available();
 

@@ -29,12 +29,15 @@
 // stripe most-significant-bit first; the order is internal to a table and
 // does not change the product.
 #include "common.cuh"
+#include "m4rm_dev.cuh"
 
 #include <mutex>
 #include <type_traits>
 
 namespace gf2 {
 namespace {
+
+using namespace m4rm_dev;
 
 constexpr int LPR = 8;          // lanes per C row
 constexpr int TILE_WORDS = 16;  // 64-bit words of C per tile row (1024 columns)
@@ -48,84 +51,6 @@ struct Params {
     int64_t groups_per_split;
     int mode;                   // 0: store, 1: C ^= (plain), 2: atomic XOR
 };
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int sz = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__host__ __device__ constexpr int ctz_c(int s) { return (s & 1) ? 0 : 1 + ctz_c(s >> 1); }
-
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
-{
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int sz = valid ? 8 : 0;
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(sz)
-                 : "memory");
-}
-
-__device__ __forceinline__ uint4 x4(uint4 a, uint4 b)
-{
-    return make_uint4(a.x ^ b.x, a.y ^ b.y, a.z ^ b.z, a.w ^ b.w);
-}
-__device__ __forceinline__ uint4 and4(uint4 a, uint4 m)
-{
-    return make_uint4(a.x & m.x, a.y & m.y, a.z & m.z, a.w & m.w);
-}
-
-// Steps s = S .. 2^LOB - 1 of the Gray-code walk of Section 3.1: entry
-// gray(s) = gray(s-1) + (row ctz(s)), one row addition per entry.  A template
-// recursion keeps every register index a compile-time constant.
-template <int S, int LOB>
-struct GrayWalk {
-    static __device__ __forceinline__ void run(uint4 &v, const uint4 (&lo)[LOB], uint4 *T, int base)
-    {
-        constexpr int j = ctz_c(S);
-        v = x4(v, lo[j]);
-        T[(base | (S ^ (S >> 1))) * LPR] = v;
-        GrayWalk<S + 1, LOB>::run(v, lo, T, base);
-    }
-};
-template <int LOB>
-struct GrayWalk<(1 << LOB), LOB> {
-    static __device__ __forceinline__ void run(uint4 &, const uint4 (&)[LOB], uint4 *, int) {}
-};
-
-// Build NT tables of 2^KB rows from KB*NT staged B rows (each 8 x 16 bytes),
-// one 16-byte column chunk per item (Section 3.1 Gray-code walk over the low
-// bits of the index, high bits combined directly).  `cmask` masks the
-// thread's column chunk (chunk == tid % 8 for every item of this thread).
-template <int KB, int NT, int NTH>
-__device__ __forceinline__ void build_tables(uint4 *tab, const uint4 *stg, int tid, uint4 cmask)
-{
-    constexpr int LOB = KB < 4 ? KB : 4;
-    constexpr int HIB = KB - LOB;
-    constexpr int TROWS = 1 << KB;
-    constexpr int ITEMS = NT * (1 << HIB) * LPR;
-#pragma unroll 1
-    for (int it = tid; it < ITEMS; it += NTH) {
-        const int c = it & 7;
-        const int hi = (it >> 3) & ((1 << HIB) - 1);
-        const int ti = it >> (3 + HIB);
-        const uint4 *S = stg + ti * KB * LPR + c;     // row j of the stripe at S[j*8]
-        uint4 lo[LOB];
-#pragma unroll
-        for (int j = 0; j < LOB; ++j) lo[j] = and4(S[j * LPR], cmask);
-        uint4 v = make_uint4(0, 0, 0, 0);
-#pragma unroll
-        for (int j = 0; j < HIB; ++j)
-            if ((hi >> j) & 1) v = x4(v, and4(S[(LOB + j) * LPR], cmask));
-        uint4 *T = tab + ti * TROWS * LPR + c;        // entry x at T[x*8]
-        const int base = hi << LOB;
-        T[base * LPR] = v;
-        GrayWalk<1, LOB>::run(v, lo, T, base);
-    }
-}
 
 template <int KB, int NT, int R, int NWARP>
 __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
@@ -205,7 +130,7 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
         cp_async_wait_all();
         __syncthreads();                       // staged rows visible; previous lookups done
         if (g + 1 < g_end) issue_stage(g + 1, buf ^ 1);
-        build_tables<KB, NT, NTH>(tab, stg + buf * KG * LPR, tid, cmask);
+        build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
         __syncthreads();                       // tables complete
         // ReadBits + AddRowFromTable for NT tables (Algorithms 1 and 3).
         const int64_t kb = (int64_t)g * KG;
@@ -303,7 +228,7 @@ __global__ void __launch_bounds__(256) make_table_kernel(DMat T, DMat B, int64_t
     const uint64_t cm0 = word_mask(cw, B.cols), cm1 = word_mask(cw + 1, B.cols);
     const uint4 cmask = make_uint4((uint32_t)cm0, (uint32_t)(cm0 >> 32), (uint32_t)cm1,
                                    (uint32_t)(cm1 >> 32));
-    build_tables<KB, 1, NTH>(tab, stg, tid, cmask);
+    build_tables<KB, 1, NTH, LPR>(tab, stg, tid, cmask);
     __syncthreads();
     for (int i = tid; i < TROWS * LPR; i += NTH) {
         const int x = i >> 3, c = i & 7;

@@ -57,7 +57,7 @@ def _mix(z: np.ndarray) -> np.ndarray:
 def splitmix64(seed: int, n: np.ndarray) -> np.ndarray:
     """Outputs number ``n`` (uint64 array, n >= 1) of the stream seeded by ``seed``."""
     with np.errstate(over="ignore"):
-        s = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + np.asarray(n, dtype=np.uint64) * GAMMA
+        s = np.uint64(int(seed) & 0xFFFFFFFFFFFFFFFF) + np.asarray(n, dtype=np.uint64) * GAMMA
         return _mix(s)
 
 
