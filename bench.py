@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of one CPU-oracle sample")
-    ap.add_argument("--workload", choices=["square", "batched"], default="square",
+    ap.add_argument("--workload", choices=["square", "batched", "chain"], default="square",
                     help="square: the n x n product (default); batched: 4096 products, "
                          "dimensions log-uniform in [64, 2048], one persistent launch")
     return ap.parse_args()
@@ -381,6 +381,52 @@ def run_batched(args, rank, world, local_rank):
     }
 
 
+def run_chain(args, rank, world, local_rank):
+    """A (131072 x 65536) . B (65536 x 131072), then . C (131072 x 8192)."""
+    import torch
+    import paper_0811_1714_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    M, K1, N1, N2 = 131072, 65536, 131072, 8192
+    A, B, AB = g.empty(M, K1), g.empty(K1, N1), g.empty(M, N1)
+    C, ABC = g.empty(N1, N2), g.empty(M, N2)
+    MA, MB, MAB, MC, MABC = g.mat(A, K1), g.mat(B, N1), g.mat(AB, N1), g.mat(C, N2), g.mat(ABC, N2)
+    g.gf2_random(MA, 31 + 100 * rank)
+    g.gf2_random(MB, 32 + 100 * rank)
+    g.gf2_random(MC, 33 + 100 * rank)
+    plans = [g.gf2_describe_plan(M, K1, N1), g.gf2_describe_plan(M, N1, N2)]
+    for _ in range(max(1, args.warmup)):
+        g.gf2_mul(MAB, MA, MB)
+        g.gf2_mul(MABC, MAB, MC)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize()
+    t1 = t2 = 0.0
+    for _ in range(args.steps):
+        ev[0].record(stream)
+        g.gf2_mul(MAB, MA, MB)
+        ev[1].record(stream)
+        g.gf2_mul(MABC, MAB, MC)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        t1 += ev[0].elapsed_time(ev[1])
+        t2 += ev[1].elapsed_time(ev[2])
+    t1 /= args.steps
+    t2 /= args.steps
+    ops1, ops2 = 2.0 * M * K1 * N1, 2.0 * M * N1 * N2
+    ok = (g.gf2_freivalds(MAB, MA, MB, 1000) == 0) and (g.gf2_freivalds(MABC, MAB, MC, 1001) == 0)
+    return {
+        "metric": "effective GF(2) bit-ops/s (2mnk/t), chain A.B then .C", "value": (ops1 + ops2) / ((t1 + t2) * 1e-3),
+        "unit": "bit-ops/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t1 + t2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "auto", "data": "synthetic: SplitMix64 Bernoulli(1/2) bits, seeds 31/32/33",
+        "config": {"workload": "chain 131072x65536 . 65536x131072 . 131072x8192", "plans": plans,
+                   "stage_ms": [t1, t2]},
+        "verified": {"freivalds_both_stages": ok},
+    }
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -395,8 +441,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload == "batched":
-        line = run_batched(args, rank, world, local_rank)
+    if args.workload in ("batched", "chain"):
+        line = (run_batched if args.workload == "batched" else run_chain)(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
