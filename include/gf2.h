@@ -105,6 +105,13 @@ int gf2_free(gf2_mat *M);
  * Device operands must all be on the current device; host operands
  * (device == GF2_HOST) are copied in and C is copied back inside the call,
  * which then returns only after the stream has finished it.
+ * Autotuning: when opts->base is GF2_BASE_AUTO and/or opts->depth is -1,
+ * accumulate is 0 and m*l*n >= 2^36, the plan comes from the autotuner: a
+ * cached choice for this (architecture, shape, options), or, on the first
+ * call, every candidate (base case x depth around the cutoff rule) is run
+ * once on these operands, timed, and the fastest is cached (in memory, and
+ * in the JSON file named by GF2_TUNE_CACHE when set).  That first call
+ * synchronises the stream.  GF2_AUTOTUNE=0 disables it (cutoff rule only).
  */
 int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B,
             const gf2_opts *opts, void *cuda_stream);

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -337,6 +338,75 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     return GF2_OK;
 }
 
+// ---------------------------------------------------------------- autotuning
+// gf2_mul with an automatic base case and/or depth on a large product
+// (m*l*n >= 2^36) asks the autotuner: a cached choice for this shape, or,
+// on the first call, every candidate (base in {M4RM, TC}, depth d0-1..d0+1
+// around the cutoff rule's d0) is timed once on the caller's operands and
+// the fastest is cached.  GF2_AUTOTUNE=0 turns this off.
+bool autotune_enabled()
+{
+    const char *e = getenv("GF2_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+std::string tune_key(int64_t m, int64_t l, int64_t n, const gf2_opts &o)
+{
+    char b[160];
+    snprintf(b, sizeof b, "mul-%s-%lldx%lldx%lld-b%d-d%d-k%d-t%d", arch_tag().c_str(), (long long)m,
+             (long long)l, (long long)n, o.base, o.depth, o.k, o.t);
+    return b;
+}
+
+// The plan(s) to run: one resolved option set, or the candidates to time.
+bool wants_tuning(int64_t m, int64_t l, int64_t n, const gf2_opts &o, std::vector<gf2_opts> *cands,
+                  std::string *key)
+{
+    cands->clear();
+    const double vol = (double)m * (double)l * (double)n;
+    const bool automatic = (o.base == GF2_BASE_AUTO || o.depth < 0);
+    if (!automatic || o.accumulate || vol < 68719476736.0 || !autotune_enabled()) {
+        cands->push_back(o);
+        return false;
+    }
+    *key = tune_key(m, l, n, o);
+    std::string v;
+    int b = 0, d = 0;
+    if (tune_get(*key, &v) && sscanf(v.c_str(), "b%dd%d", &b, &d) == 2) {
+        gf2_opts r = o;
+        r.base = b;
+        r.depth = d;
+        cands->push_back(r);
+        return false;
+    }
+    std::vector<int> bases;
+    if (o.base != GF2_BASE_AUTO) bases.push_back(o.base);
+    else {
+        bases.push_back(GF2_BASE_M4RM);
+        if (tc_fp8_available()) bases.push_back(GF2_BASE_TC_FP8);
+    }
+    for (int base : bases) {
+        std::vector<int> depths;
+        if (o.depth >= 0) depths.push_back(o.depth);
+        else {
+            const int d0 = auto_depth(m, l, n, base);
+            for (int d = d0 - 1; d <= d0 + 1; ++d) {
+                const int64_t mn = std::min(m, std::min(l, n));
+                if (d < 0 || d > 6 || (mn >> d) < 1024) continue;
+                depths.push_back(d);
+            }
+        }
+        for (int d : depths) {
+            gf2_opts r = o;
+            r.base = base;
+            r.depth = d;
+            cands->push_back(r);
+        }
+    }
+    if (cands->size() <= 1) return false;
+    return true;
+}
+
 size_t staged_bytes(const gf2_mat *M)
 {
     return (size_t)(M->rows * even_up(words_of(M->cols))) * 8;
@@ -457,11 +527,15 @@ int gf2_describe_plan(int64_t m, int64_t l, int64_t n, const gf2_opts *opts, cha
     if (m < 0 || l < 0 || n < 0) return GF2_EINVAL;
     int rc = check_opts(o);
     if (rc) return rc;
+    std::vector<gf2_opts> cands;
+    std::string key;
+    gf2_opts eff = o;
+    if (!wants_tuning(m, l, n, o, &cands, &key)) eff = cands[0];
     Plan p;
-    rc = make_plan(m, l, n, o, &p);
+    rc = make_plan(m, l, n, eff, &p);
     if (rc) return rc;
     std::string t = plan_text(p);
-    if (o.base != GF2_BASE_TC_FP8 && m > 0 && n > 0) {
+    if (p.base != GF2_BASE_TC_FP8 && m > 0 && n > 0) {
         int k = o.k, tt = o.t, bm = 0, ks = 0;
         const int d = p.depth;
         int batch = 1;
@@ -544,11 +618,19 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
         if (M->device != GF2_HOST && M->device != dev && M->rows && M->cols) return GF2_EINVAL;
 
     const int64_t m = A->rows, l = A->cols, n = B->cols;
-    Plan p;
-    if ((rc = make_plan(m, l, n, o, &p))) return rc;
+    // candidate plans: one, or several when the autotuner picks base / depth
+    std::vector<gf2_opts> cands;
+    std::string tkey;
+    const bool tuning = wants_tuning(m, l, n, o, &cands, &tkey);
+    std::vector<Plan> plans(cands.size());
+    size_t most = 0;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if ((rc = make_plan(m, l, n, cands[i], &plans[i]))) return rc;
+        most = std::max(most, plans[i].bytes);
+    }
 
     const bool hA = A->device == GF2_HOST, hB = B->device == GF2_HOST, hC = C->device == GF2_HOST;
-    size_t total = p.bytes;
+    size_t total = (most + 255) & ~(size_t)255;
     size_t offA = total, offB = 0, offC = 0;
     if (hA) { offA = total; total += (staged_bytes(A) + 255) & ~(size_t)255; }
     if (hB) { offB = total; total += (staged_bytes(B) + 255) & ~(size_t)255; }
@@ -580,8 +662,37 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
             GF2_CUDA_TRY(cudaMemcpy2DAsync(dC.data, dC.stride_words * 8, C->data, C->stride_words * 8,
                                            words_of(n) * 8, m, cudaMemcpyHostToDevice, s));
     }
-    rc = mul_device(&dC, &dA, &dB, p, o.accumulate, base, s);
-    if (rc) return rc;
+    if (!tuning) {
+        rc = mul_device(&dC, &dA, &dB, plans[0], o.accumulate, base, s);
+        if (rc) return rc;
+    } else {
+        // time every candidate on these operands (each computes the same C)
+        cudaEvent_t e0, e1;
+        GF2_CUDA_TRY(cudaEventCreate(&e0));
+        GF2_CUDA_TRY(cudaEventCreate(&e1));
+        size_t best = 0;
+        float best_ms = 1e30f;
+        for (size_t i = 0; i < plans.size(); ++i) {
+            cudaEventRecord(e0, s);
+            rc = mul_device(&dC, &dA, &dB, plans[i], 0, base, s);
+            cudaEventRecord(e1, s);
+            float ms = 1e30f;
+            if (rc == GF2_OK && cudaEventSynchronize(e1) == cudaSuccess)
+                cudaEventElapsedTime(&ms, e0, e1);
+            if (rc == GF2_OK && ms < best_ms) { best_ms = ms; best = i; }
+            if (rc) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc) return rc;
+        if (best + 1 != plans.size()) {     // leave the chosen plan's result, as a plain call would
+            rc = mul_device(&dC, &dA, &dB, plans[best], 0, base, s);
+            if (rc) return rc;
+        }
+        char v[32];
+        snprintf(v, sizeof v, "b%dd%d", plans[best].base, plans[best].depth);
+        tune_put(tkey, v);
+    }
     if (hC && m && n) {
         GF2_CUDA_TRY(cudaMemcpy2DAsync(C->data, C->stride_words * 8, dC.data, dC.stride_words * 8,
                                        words_of(n) * 8, m, cudaMemcpyDeviceToHost, s));

@@ -270,51 +270,9 @@ std::string signature(const std::vector<BProd> &prods, int accumulate)
         h ^= k;
         h *= 1099511628211ull;
     }
-    int dev = 0, major = 0, minor = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
     char buf[96];
-    snprintf(buf, sizeof buf, "sm%d%d-n%zu-a%d-%016llx", major, minor, prods.size(), accumulate, h);
+    snprintf(buf, sizeof buf, "batched-%s-n%zu-a%d-%016llx", arch_tag().c_str(), prods.size(), accumulate, h);
     return buf;
-}
-
-// ------------------------------------------------------------------ tune cache
-std::mutex g_mu;
-std::map<std::string, std::string> g_tuned;   // signature -> variant name
-bool g_tuned_loaded = false;
-
-void load_tune_cache()
-{
-    if (g_tuned_loaded) return;
-    g_tuned_loaded = true;
-    const char *path = getenv("GF2_TUNE_CACHE");
-    if (!path || !*path) return;
-    FILE *f = fopen(path, "r");
-    if (!f) return;
-    char line[512];
-    // one entry per line: "signature": "variant",
-    while (fgets(line, sizeof line, f)) {
-        char k[256], v[128];
-        if (sscanf(line, " \"%255[^\"]\" : \"%127[^\"]\"", k, v) == 2) g_tuned[k] = v;
-    }
-    fclose(f);
-}
-
-void save_tune_cache()
-{
-    const char *path = getenv("GF2_TUNE_CACHE");
-    if (!path || !*path) return;
-    std::string tmp = std::string(path) + ".tmp";
-    FILE *f = fopen(tmp.c_str(), "w");
-    if (!f) return;
-    fprintf(f, "{\n");
-    size_t i = 0;
-    for (const auto &kv : g_tuned)
-        fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kv.second.c_str(), ++i < g_tuned.size() ? "," : "");
-    fprintf(f, "}\n");
-    fclose(f);
-    rename(tmp.c_str(), path);
 }
 
 // ------------------------------------------------------------------ graphs
@@ -326,6 +284,7 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int ntiles = 0;
 };
+std::mutex g_mu;
 std::list<GraphEntry> g_graphs;             // most recently used first
 constexpr size_t kMaxGraphs = 8;
 
@@ -467,17 +426,15 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
     const auto &vs = bvariants();
     int vi = force_variant;
     if (vi < 0 || vi >= (int)vs.size()) {
-        load_tune_cache();
         const std::string sig = signature(prods, accumulate);
-        auto f = g_tuned.find(sig);
+        std::string name;
         vi = -1;
-        if (f != g_tuned.end())
+        if (tune_get(sig, &name))
             for (size_t i = 0; i < vs.size(); ++i)
-                if (f->second == vs[i].name) vi = (int)i;
+                if (name == vs[i].name) vi = (int)i;
         if (vi < 0) {
             vi = autotune(prods, accumulate, s);
-            g_tuned[sig] = vs[vi].name;
-            save_tune_cache();
+            tune_put(sig, vs[vi].name);
         }
     }
     const BVariant &v = vs[vi];

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "gf2.h"
 
 namespace gf2 {
@@ -123,6 +125,11 @@ struct TcLaunch {
     unsigned int *status;                    // device word for timeouts (may be null)
 };
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
+
+// Autotuner cache (tune.cu): text signature -> text choice.
+bool tune_get(const std::string &key, std::string *value);
+void tune_put(const std::string &key, const std::string &value);
+std::string arch_tag();
 
 // Batched persistent M4RM (one launch, graph-replayed, autotuned).
 int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[], int count,
