@@ -96,9 +96,14 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
 
-    // Stage pass g: its KG rows of B (tile columns) and the 1-2 words of each
-    // tile row of A that hold columns g*KG .. g*KG+KG-1.
-    auto issue_stage = [&](int g, int buf) {
+    // Stage pass g: its KG rows of B (tile columns) and the words of each
+    // tile row of A that hold columns g*KG .. g*KG+KG-1.  When KG divides 128
+    // (CHUNKED_A), A is staged one aligned 16-byte chunk per row (128
+    // columns = 128/KG passes) at the first pass of the previous chunk;
+    // otherwise the 1-2 words of every pass are staged with the pass.
+    constexpr bool CHUNKED_A = (128 % KG) == 0;
+    constexpr int PPC = CHUNKED_A ? 128 / KG : 1;          // passes per A chunk
+    auto issue_stage = [&](int g, int buf, bool a_chunk) {
 #pragma unroll 1
         for (int i = tid; i < KG * LPR; i += NTH) {
             const int rr = i >> 3, cc = i & 7;
@@ -107,29 +112,48 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
             const bool valid = (brow < P.l) && (bw < nW);
             cp_async16(&stg[buf * KG * LPR + i], valid ? (B + brow * P.ldb + bw) : B, valid);
         }
-        const int64_t kb = (int64_t)g * KG;
-        const int64_t wa = kb >> 6;
-        const bool two = ((kb & 63) + KG > 64) && (wa + 1 < lW);
+        if (CHUNKED_A) {
+            if (a_chunk) {
+                const int c = g / PPC;                    // A chunk holding pass g
+                const int64_t wa = 2 * (int64_t)c;
+                const int abuf = c & 1;
 #pragma unroll 1
-        for (int i = tid; i < BM; i += NTH) {
-            const int64_t row = row0 + i;
-            const bool valid = row < P.m;
-            const uint64_t *src = A + (valid ? row * P.lda + wa : 0);
-            uint4 *dst = &sta[buf * BM + i];
-            cp_async8(dst, src, valid);
-            if (two) cp_async8(reinterpret_cast<char *>(dst) + 8, src + 1, valid);
+                for (int i = tid; i < BM; i += NTH) {
+                    const int64_t row = row0 + i;
+                    const bool valid = (row < P.m) && (wa < lW);
+                    cp_async16(&sta[abuf * BM + i], A + (valid ? row * P.lda + wa : 0), valid);
+                }
+            }
+        } else {
+            const int64_t kb = (int64_t)g * KG;
+            const int64_t wa = kb >> 6;
+            const bool two = ((kb & 63) + KG > 64) && (wa + 1 < lW);
+#pragma unroll 1
+            for (int i = tid; i < BM; i += NTH) {
+                const int64_t row = row0 + i;
+                const bool valid = row < P.m;
+                const uint64_t *src = A + (valid ? row * P.lda + wa : 0);
+                uint4 *dst = &sta[buf * BM + i];
+                cp_async8(dst, src, valid);
+                if (two) cp_async8(reinterpret_cast<char *>(dst) + 8, src + 1, valid);
+            }
         }
         cp_async_commit();
     };
 
-    if (g_begin < g_end) issue_stage(g_begin, 0);
+    // the first pass stages the A chunk holding it (a K split may start
+    // inside a chunk); every later chunk is staged one pass before its first
+    if (g_begin < g_end) issue_stage(g_begin, 0, true);
 
 #pragma unroll 1
     for (int g = g_begin; g < g_end; ++g) {
         const int buf = (g - g_begin) & 1;
         cp_async_wait_all();
         __syncthreads();                       // staged rows visible; previous lookups done
-        if (g + 1 < g_end) issue_stage(g + 1, buf ^ 1);
+        if (g + 1 < g_end) {
+            const bool next_chunk = CHUNKED_A && ((g + 1) % PPC) == 0;
+            issue_stage(g + 1, buf ^ 1, next_chunk);
+        }
         build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
         __syncthreads();                       // tables complete
         // ReadBits + AddRowFromTable for NT tables (Algorithms 1 and 3).
@@ -138,13 +162,14 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
         const int sh = (int)(kb & 63);
         const uint64_t mlo = word_mask(wa, P.l);
         const uint64_t mhi = (sh + KG > 64) ? word_mask(wa + 1, P.l) : 0ull;
-        const uint4 *arow = sta + buf * BM + trow;
+        const uint4 *arow = sta + (CHUNKED_A ? ((g / PPC) & 1) : buf) * BM + trow;
+        const int aoff = CHUNKED_A ? (int)(wa & 1) : 0;          // word inside the staged chunk
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const uint2 aw = *reinterpret_cast<const uint2 *>(&arow[4 * r]);
+            const uint2 aw = reinterpret_cast<const uint2 *>(&arow[4 * r])[aoff];
             const uint64_t lo = ((uint64_t)aw.y << 32 | aw.x) & mlo;
             uint64_t bits = lo >> sh;
-            if (sh + KG > 64) {
+            if (!CHUNKED_A && sh + KG > 64) {
                 const uint2 aw2 = reinterpret_cast<const uint2 *>(&arow[4 * r])[1];
                 bits |= (((uint64_t)aw2.y << 32 | aw2.x) & mhi) << (64 - sh);
             }
