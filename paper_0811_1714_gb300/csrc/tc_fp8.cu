@@ -12,23 +12,30 @@
 // ulp is 2^-12); parities of successive chunks are XORed, which is the
 // GF(2) sum over the whole K range.
 //
-// Layout of one CTA (persistent, one per SM, 17 warps):
-//   warps 0-3  epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator (warp w
-//              reads TMEM lanes 32w..32w+31 = rows of the tile), parity,
-//              packed 64-bit words of C;
-//   warp 4     TMEM allocation (512 columns = two accumulators) and the MMA
-//              issuer (one thread): tcgen05.mma.cta_group::1.kind::f8f6f4,
-//              M = 128, N = 256, K = 32 per instruction;
-//   warps 5-16 producers: read the packed words of A (128 rows) and B^T (256
-//              rows) for a 128-entry K block, expand every bit to one FP8
-//              byte and store the tile in the 128-byte-swizzled K-major
-//              layout the MMA reads (4 stages of 48 KB in shared memory).
-// Hand-offs use mbarriers: full/empty per stage (producers <-> MMA, the MMA
-// side signalled by tcgen05.commit) and full/empty per accumulator
-// (MMA <-> epilogue).  Every wait is bounded; an expired wait records
-// GF2_ETIMEOUT in a device status word and the CTA winds down (waits for
-// its issued MMAs, frees its tensor memory) instead of hanging.
+// Layout of one CTA (persistent, one per SM, 18 warps):
+//   warps 0-3   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator (warp
+//               w reads TMEM lanes 32w..32w+31 = rows of the tile), parity,
+//               packed 64-bit words of C;
+//   warp 4      TMEM allocation (512 columns = two accumulators) and the MMA
+//               issuer (one thread): tcgen05.mma.cta_group::1.kind::f8f6f4,
+//               M = 128, N = 256, K = 32 per instruction;
+//   warp 5      TMA issuer (one thread): cp.async.bulk.tensor loads of the
+//               PACKED words of A (128 rows x 16 bytes) and B^T (256 rows x
+//               16 bytes) of a 128-entry K block into a ring of packed stages
+//               (rows beyond the matrices and words beyond K arrive as zeros);
+//   warps 6-17  unpackers: read a packed stage, expand every bit to one FP8
+//               byte (a byte of bits -> 8 FP8 bytes through a bank-conflict-
+//               free table in shared memory) and store the tile in the
+//               128-byte-swizzled K-major layout the MMA reads.
+// Hand-offs use mbarriers: packed full (TMA transaction bytes) / packed empty,
+// unpacked full / empty (the MMA side signalled by tcgen05.commit), and
+// accumulator full / empty (MMA <-> epilogue).  Every wait is bounded; an
+// expired wait records GF2_ETIMEOUT in a device status word and the CTA winds
+// down (waits for its issued copies and MMAs, frees its tensor memory)
+// instead of hanging.
 #include "common.cuh"
+
+#include <cuda.h>
 
 #include <mutex>
 
@@ -38,21 +45,38 @@ namespace {
 constexpr int BM = 128;            // rows of A per tile (MMA M)
 constexpr int BN = 256;            // rows of B^T per tile (MMA N)
 constexpr int BK = 128;            // K entries per stage (128 FP8 bytes = one swizzle row)
-constexpr int STAGES = 4;
+constexpr int USTAGES = 3;         // unpacked (FP8) stages
+constexpr int PSTAGES = 8;         // packed stages
 constexpr int KCHUNK = 4096;       // exact-sum bound (entries per accumulation)
 constexpr int KB_PER_CHUNK = KCHUNK / BK;
 constexpr int A_BYTES = BM * BK;   // 16 KB
 constexpr int B_BYTES = BN * BK;   // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int PA_BYTES = BM * 16;  // packed A block: 128 rows x 2 words
+constexpr int PB_BYTES = BN * 16;  // packed B^T block: 256 rows x 2 words
+constexpr int PSTAGE_BYTES = PA_BYTES + PB_BYTES;
 constexpr int NUM_EPI_WARPS = 4;
 constexpr int MMA_WARP = 4;
-constexpr int NUM_PROD_WARPS = 12;
-constexpr int PROD_WARP0 = 5;
-constexpr int NTHREADS = (PROD_WARP0 + NUM_PROD_WARPS) * 32;   // 544
-constexpr int NPROD = NUM_PROD_WARPS * 32;                      // 384
-constexpr int PROD_ROWS = (2 * (BM + BN) + NPROD - 1) / NPROD;   // half rows per producer thread
+constexpr int TMA_WARP = 5;
+constexpr int NUM_UNP_WARPS = 12;
+constexpr int UNP_WARP0 = 6;
+constexpr int NTHREADS = (UNP_WARP0 + NUM_UNP_WARPS) * 32;     // 576
+constexpr int NUNP = NUM_UNP_WARPS * 32;                        // 384
+constexpr int UNP_ROWS = (2 * (BM + BN) + NUNP - 1) / NUNP;     // half rows per unpacker thread
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;        // clock64 cycles (~2 s)
+
+// Byte -> 8 FP8 bytes through a table in shared memory: 256 entries of 8
+// bytes, replicated 16 times and interleaved (entry e of copy j at 8-byte
+// slot 16e + j) so that lane j of a half-warp always reads bank pair j:
+// conflict free whatever the bytes are.
+constexpr int LUT_COPIES = 16;
+constexpr int LUT_BYTES = 256 * LUT_COPIES * 8;   // 32 KB
+
+// barriers: pfull[P], pempty[P], ufull[U], uempty[U], tfull[2], tempty[2], done
+constexpr int NBARS = 2 * PSTAGES + 2 * USTAGES + 5;
+constexpr int SMEM_BYTES = USTAGES * STAGE_BYTES + PSTAGES * PSTAGE_BYTES + LUT_BYTES + NBARS * 8 + 16 + 1024;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
 // FP8 E4M3 0x08 = 2^-6: a 1-bit.  Instruction descriptor (kind::f8f6f4):
 // D format F32 (bits 4-5 = 1), A = B = E4M3 (bits 7-9, 10-12 = 0), both
@@ -60,13 +84,11 @@ constexpr unsigned long long WAIT_LIMIT = 4000000000ull;        // clock64 cycle
 constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 struct Params {
-    const uint64_t *A; int64_t lda, bsA;
-    const uint64_t *Bt; int64_t ldb, bsB;
-    uint64_t *C; int64_t ldc, bsC;
     int64_t m, l, n;
-    int batch;
     int tiles_m, tiles_n;
     int64_t tiles;
+    uint64_t *C;
+    int64_t ldc, bsC;
     int accumulate;
     unsigned int *status;
 };
@@ -84,6 +106,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
@@ -116,6 +143,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
     }
 }
 
+// Bounded wait that ignores the abort flag (used to drain copies in flight).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity, unsigned int *status)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if ((unsigned long long)(clock64() - t0) > WAIT_LIMIT) {
+            if (status) atomicExch(status, (unsigned int)(-GF2_ETIMEOUT));
+            return;
+        }
+    }
+}
+
 // Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast, so all
 // lanes leave together (the warp-collective tcgen05 instructions that
 // follow need every lane).
@@ -135,6 +174,14 @@ __device__ __forceinline__ bool warp_aborted(volatile int *abort_flag)
     int a = 0;
     if ((threadIdx.x & 31) == 0) a = *abort_flag;
     return __shfl_sync(0xffffffffu, a, 0) != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
@@ -195,31 +242,39 @@ __device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, 
     tn = (int)(r - (int64_t)tm * P.tiles_n);
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
+__global__ void __launch_bounds__(NTHREADS, 1)
+tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Params P)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // stage buffers must sit on 1024-byte boundaries (128-byte swizzle atoms)
+    // unpacked stages must sit on 1024-byte boundaries (128-byte swizzle atoms)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *sbase = smem_raw + (base - raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sbase + STAGES * STAGE_BYTES);
-    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], done
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+    unsigned char *pbase = sbase + USTAGES * STAGE_BYTES;                    // packed ring
+    uint2 *lut = reinterpret_cast<uint2 *>(pbase + PSTAGES * PSTAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(lut) + LUT_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
-    auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
-    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
-    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
-    const uint32_t done_bar = bar0 + 8u * (2 * STAGES + 4);
+    auto pfull_bar = [&](int s) { return bar0 + 8u * s; };
+    auto pempty_bar = [&](int s) { return bar0 + 8u * (PSTAGES + s); };
+    auto ufull_bar = [&](int s) { return bar0 + 8u * (2 * PSTAGES + s); };
+    auto uempty_bar = [&](int s) { return bar0 + 8u * (2 * PSTAGES + USTAGES + s); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * USTAGES + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * USTAGES + 2 + b); };
+    const uint32_t done_bar = bar0 + 8u * (2 * PSTAGES + 2 * USTAGES + 4);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full_bar(s), NPROD);
-            mbar_init(empty_bar(s), 1);
+        for (int s = 0; s < PSTAGES; ++s) {
+            mbar_init(pfull_bar(s), 1);                   // the TMA thread's expect_tx arrival
+            mbar_init(pempty_bar(s), NUM_UNP_WARPS);
+        }
+        for (int s = 0; s < USTAGES; ++s) {
+            mbar_init(ufull_bar(s), NUM_UNP_WARPS);       // one arrival per unpacker warp
+            mbar_init(uempty_bar(s), 1);                  // tcgen05.commit
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull_bar(b), 1);
@@ -229,6 +284,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < 256 * LUT_COPIES; i += NTHREADS) {
+        const uint32_t e = (uint32_t)(i / LUT_COPIES);
+        lut[i] = make_uint2(spread4(e & 0xF), spread4(e >> 4));
     }
     if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -242,97 +301,81 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
 
     const int64_t nkb = (P.l + BK - 1) / BK;            // K blocks per tile
     const int nchunks = (int)((nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
+    const int64_t my_tiles = (P.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const int64_t Q = my_tiles * nkb;                    // stage uses of this CTA, in (tile, K block) order
 
-    if (warp >= PROD_WARP0) {
-        // ------------------------------------------------------------ producers
-        // The CTA's stage uses form one sequence q = 0..Q-1 over (tile, K
-        // block); each thread keeps the packed words of the next PREF uses in
-        // registers so that global-load latency hides behind PREF stages.
-        const int pt = threadIdx.x - PROD_WARP0 * 32;     // 0..NPROD-1
-        const int64_t lW = words_of(P.l);
-        const int64_t my_tiles = (P.tiles - blockIdx.x + gridDim.x - 1) / gridDim.x;
-        const int64_t Q = my_tiles * nkb;
-        // load cursor: the (tile, K block) of the next use to be loaded
-        int64_t cur_q = 0, cur_t = blockIdx.x, cur_kb = 0;
-        const uint64_t *cur_a = nullptr, *cur_b = nullptr;
-        int64_t cur_rowa = 0, cur_rowb = 0;
-        auto set_tile = [&]() {
-            int b, tm, tn;
-            tile_coords(P, cur_t, b, tm, tn);
-            cur_a = P.A + (int64_t)b * P.bsA;
-            cur_b = P.Bt + (int64_t)b * P.bsB;
-            cur_rowa = (int64_t)tm * BM;
-            cur_rowb = (int64_t)tn * BN;
-        };
-        if (Q > 0) set_tile();
-        auto load_use = [&](uint64_t (&w)[PROD_ROWS]) {
+    if (warp == TMA_WARP) {
+        // ------------------------------------------------------------ TMA issuer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+            int64_t t = blockIdx.x, kb = 0;
+            int b = 0, tm = 0, tn = 0;
+            if (Q > 0) tile_coords(P, t, b, tm, tn);
+            int64_t q = 0;
+            for (; q < Q; ++q) {
+                const int ps = (int)(q % PSTAGES);
+                if (!mbar_wait(pempty_bar(ps), (uint32_t)((q / PSTAGES) & 1) ^ 1u, P.status, abort_flag)) break;
+                const uint32_t dst = smem_u32(pbase + ps * PSTAGE_BYTES);
+                mbar_arrive_expect_tx(pfull_bar(ps), PSTAGE_BYTES);
+                tma_load_3d(dst, &mapA, (int)(kb * 2), tm * BM, b, pfull_bar(ps));
+                tma_load_3d(dst + PA_BYTES, &mapB, (int)(kb * 2), tn * BN, b, pfull_bar(ps));
+                if (++kb == nkb) {
+                    kb = 0;
+                    t += gridDim.x;
+                    if (q + 1 < Q) tile_coords(P, t, b, tm, tn);
+                }
+            }
+            // wind down: copies issued but not consumed (only after an abort)
+            // still land in shared memory; wait for them before the CTA exits
+            for (int64_t r = (q > PSTAGES ? q - PSTAGES : 0); r < q; ++r)
+                mbar_drain(pfull_bar((int)(r % PSTAGES)), (uint32_t)((r / PSTAGES) & 1), P.status);
+        }
+        __syncwarp();
+    } else if (warp >= UNP_WARP0) {
+        // ------------------------------------------------------------ unpackers
+        const int pt = threadIdx.x - UNP_WARP0 * 32;      // 0..NUNP-1
+        const uint2 *lutl = lut + (lane & (LUT_COPIES - 1));
+        int64_t kb = 0;
+        for (int64_t q = 0; q < Q; ++q) {
+            const int ps = (int)(q % PSTAGES);
+            const int us = (int)(q % USTAGES);
+            if (!warp_wait(pfull_bar(ps), (uint32_t)((q / PSTAGES) & 1), P.status, abort_flag)) break;
+            if (!warp_wait(uempty_bar(us), (uint32_t)((q / USTAGES) & 1) ^ 1u, P.status, abort_flag)) break;
+            const unsigned char *pk = pbase + ps * PSTAGE_BYTES;   // A rows then B^T rows, 16 bytes each
+            unsigned char *st = sbase + us * STAGE_BYTES;
 #pragma unroll
-            for (int j = 0; j < PROD_ROWS; ++j) w[j] = 0;
-            if (cur_q >= Q) return;
-#pragma unroll
-            for (int j = 0; j < PROD_ROWS; ++j) {
-                const int hr = pt + j * NPROD;             // half rows: 256 of A, 512 of B^T
+            for (int j = 0; j < UNP_ROWS; ++j) {
+                const int hr = pt + j * NUNP;              // half rows: 256 of A, then 512 of B^T
                 if (hr >= 2 * (BM + BN)) continue;
                 const int row = hr >> 1, half = hr & 1;
-                const int64_t wi = cur_kb * 2 + half;
-                if (wi >= lW) continue;
-                if (row < BM) {
-                    const int64_t gr = cur_rowa + row;
-                    if (gr < P.m) w[j] = __ldg(cur_a + gr * P.lda + wi) & word_mask(wi, P.l);
-                } else {
-                    const int64_t gr = cur_rowb + (row - BM);
-                    if (gr < P.n) w[j] = __ldg(cur_b + gr * P.ldb + wi) & word_mask(wi, P.l);
+                // words beyond K arrive as zeros; bits beyond K in the last word are masked
+                const uint64_t wv = reinterpret_cast<const uint64_t *>(pk)[hr] & word_mask(kb * 2 + half, P.l);
+                unsigned char *rowp = (row < BM) ? (st + (row >> 3) * 1024 + (row & 7) * 128)
+                                                 : (st + A_BYTES + ((row - BM) >> 3) * 1024 + ((row - BM) & 7) * 128);
+                const int sw = row & 7;                    // (row - BM) & 7 == row & 7
+                const uint32_t lo = (uint32_t)wv, hi = (uint32_t)(wv >> 32);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {            // 16 entries -> one 16-byte chunk
+                    const uint32_t bits = qq < 2 ? lo : hi;
+                    const uint32_t b0 = __byte_perm(bits, 0, 0x4440 | ((qq & 1) * 2));
+                    const uint32_t b1 = __byte_perm(bits, 0, 0x4441 | ((qq & 1) * 2));
+                    const uint2 e0 = lutl[b0 * LUT_COPIES];
+                    const uint2 e1 = lutl[b1 * LUT_COPIES];
+                    const int chunk = (half * 4 + qq) ^ sw; // 128-byte swizzle
+                    *reinterpret_cast<uint4 *>(rowp + chunk * 16) = make_uint4(e0.x, e0.y, e1.x, e1.y);
                 }
             }
-            ++cur_q;
-            if (++cur_kb == nkb) {
-                cur_kb = 0;
-                cur_t += gridDim.x;
-                if (cur_q < Q) set_tile();
+            // each lane makes its stores visible to the tensor core (async
+            // proxy), then one arrival per warp on the unpacked stage, and
+            // the packed stage is handed back to the TMA thread
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(ufull_bar(us));
+                mbar_arrive(pempty_bar(ps));
             }
-        };
-        constexpr int PREF = 4;
-        uint64_t pre[PREF][PROD_ROWS];
-#pragma unroll
-        for (int d = 0; d < PREF; ++d) load_use(pre[d]);
-        bool ok = true;
-        for (int64_t q0 = 0; q0 < Q && ok; q0 += PREF) {
-#pragma unroll
-            for (int d = 0; d < PREF; ++d) {
-                const int64_t q = q0 + d;
-                if (q >= Q) break;
-                const uint32_t it = (uint32_t)q;
-                const int s = (int)(it % STAGES);
-                const uint32_t ph = (it / STAGES) & 1u;
-                if (!warp_wait(empty_bar(s), ph ^ 1u, P.status, abort_flag)) { ok = false; break; }
-                unsigned char *st = sbase + s * STAGE_BYTES;
-#pragma unroll
-                for (int j = 0; j < PROD_ROWS; ++j) {
-                    const int hr = pt + j * NPROD;
-                    if (hr >= 2 * (BM + BN)) continue;
-                    const int row = hr >> 1, half = hr & 1;
-                    // row r of the A block, or row r-128 of the B block
-                    unsigned char *rowp = (row < BM) ? (st + (row >> 3) * 1024 + (row & 7) * 128)
-                                                     : (st + A_BYTES + ((row - BM) >> 3) * 1024 +
-                                                        ((row - BM) & 7) * 128);
-                    const int sw = row & 7;                    // (row - BM) & 7 == row & 7
-                    const uint32_t lo = (uint32_t)pre[d][j], hi = (uint32_t)(pre[d][j] >> 32);
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {            // 16 entries -> one 16-byte chunk
-                        const uint32_t bits = (qq < 2 ? lo : hi) >> ((qq & 1) * 16);
-                        uint4 v;
-                        v.x = spread4(bits & 0xF);
-                        v.y = spread4((bits >> 4) & 0xF);
-                        v.z = spread4((bits >> 8) & 0xF);
-                        v.w = spread4((bits >> 12) & 0xF);
-                        const int chunk = (half * 4 + qq) ^ sw; // 128-byte swizzle
-                        *reinterpret_cast<uint4 *>(rowp + chunk * 16) = v;
-                    }
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(full_bar(s));
-                load_use(pre[d]);
-            }
+            if (++kb == nkb) kb = 0;
         }
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
@@ -348,8 +391,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
                     const int64_t kb0 = (int64_t)c * KB_PER_CHUNK;
                     const int64_t kb1 = min(nkb, kb0 + KB_PER_CHUNK);
                     for (int64_t kb = kb0; kb < kb1; ++kb, ++it) {
-                        const int s = (int)(it % STAGES);
-                        if (!mbar_wait(full_bar(s), (it / STAGES) & 1u, P.status, abort_flag)) { ok = false; break; }
+                        const int s = (int)(it % USTAGES);
+                        if (!mbar_wait(ufull_bar(s), (it / USTAGES) & 1u, P.status, abort_flag)) { ok = false; break; }
                         tc_fence_after();
                         const uint32_t sa = base + s * STAGE_BYTES;
                         const uint32_t sb = sa + A_BYTES;
@@ -359,7 +402,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
                             mma_f8(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
                                    (kb > kb0 || kk > 0) ? 1u : 0u);
                         }
-                        mma_commit(empty_bar(s));          // stage free once these MMAs have read it
+                        mma_commit(uempty_bar(s));         // stage free once these MMAs have read it
                     }
                     if (!ok) break;
                     mma_commit(tfull_bar(ab));             // accumulator ready for the epilogue
@@ -367,13 +410,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
             }
             // wind down: wait until every issued MMA has completed
             mma_commit(done_bar);
-            const long long t0 = clock64();
-            while (!mbar_try_wait(done_bar, 0)) {
-                if ((unsigned long long)(clock64() - t0) > WAIT_LIMIT) {
-                    if (P.status) atomicExch(P.status, (unsigned int)(-GF2_ETIMEOUT));
-                    break;
-                }
-            }
+            mbar_drain(done_bar, 0, P.status);
         }
         __syncwarp();
     } else {
@@ -435,9 +472,48 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_fp8_kernel(Params P)
     }
 }
 
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-
 __device__ unsigned int g_tc_status;   // -GF2_ETIMEOUT after an expired wait
+
+// cuTensorMapEncodeTiled from the driver, looked up once (no link-time
+// dependency on the driver library).
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn()
+{
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D map over packed words: x = word in the row (extent ceil(l/64): words
+// beyond K are filled with zeros), y = row (extent rows), z = product of the
+// batch.  Box: 2 words x box_rows x 1.
+int make_map(CUtensorMap *map, const uint64_t *base, int64_t words, int64_t rows, int64_t ld, int batch,
+             int64_t bs, int box_rows)
+{
+    EncodeFn fn = encode_fn();
+    if (!fn) return GF2_EUNSUPPORTED;
+    const cuuint64_t dims[3] = {(cuuint64_t)words, (cuuint64_t)rows, (cuuint64_t)batch};
+    const int64_t bstride = batch > 1 ? bs * 8 : rows * ld * 8;
+    const cuuint64_t strides[2] = {(cuuint64_t)(ld * 8), (cuuint64_t)(bstride > 0 ? bstride : ld * 8)};
+    const cuuint32_t box[3] = {2u, (cuuint32_t)box_rows, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<uint64_t *>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GF2_OK : GF2_ECUDA;
+}
 
 }  // namespace
 
@@ -450,7 +526,7 @@ bool tc_fp8_available()
         cudaGetLastError();
         return false;
     }
-    return major == 10 && minor == 3;     // built for sm_103a only
+    return major == 10 && minor == 3 && encode_fn() != nullptr;     // built for sm_103a only
 }
 
 int tc_status_read_and_clear(unsigned int *out, cudaStream_t s)
@@ -468,19 +544,26 @@ int tc_status_read_and_clear(unsigned int *out, cudaStream_t s)
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s)
 {
     if (L.batch <= 0 || L.m <= 0 || L.n <= 0) return GF2_OK;
+    // operand rows must start on 16-byte boundaries for the tensor copies
+    if ((L.lda & 1) || (L.ldb & 1) || (reinterpret_cast<uintptr_t>(L.A) & 15) ||
+        (reinterpret_cast<uintptr_t>(L.Bt) & 15) || (L.batch > 1 && ((L.bsA & 1) || (L.bsB & 1))))
+        return GF2_ELAYOUT;
+    if (L.m > INT32_MAX || L.n > INT32_MAX || words_of(L.l) > INT32_MAX || L.batch > 65535) return GF2_EUNSUPPORTED;
     Params P;
-    P.A = L.A; P.lda = L.lda; P.bsA = L.bsA;
-    P.Bt = L.Bt; P.ldb = L.ldb; P.bsB = L.bsB;
-    P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
     P.m = L.m; P.l = L.l; P.n = L.n;
-    P.batch = L.batch;
     P.tiles_m = div_up(L.m, BM);
     P.tiles_n = div_up(L.n, BN);
     P.tiles = (int64_t)L.batch * P.tiles_m * P.tiles_n;
+    P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
     P.accumulate = L.accumulate;
     unsigned int *st = L.status;
     if (!st) GF2_CUDA_TRY(cudaGetSymbolAddress((void **)&st, g_tc_status));
     P.status = st;
+    CUtensorMap mapA, mapB;
+    int rc = make_map(&mapA, L.A, words_of(L.l), L.m, L.lda, L.batch, L.bsA, BM);
+    if (rc) return rc;
+    rc = make_map(&mapB, L.Bt, words_of(L.l), L.n, L.ldb, L.batch, L.bsB, BN);
+    if (rc) return rc;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
@@ -492,7 +575,7 @@ int tc_fp8_launch(const TcLaunch &L, cudaStream_t s)
     GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t grid = P.tiles < sms ? P.tiles : sms;
     ProfScope ps(PF_TC, s);
-    tc_fp8_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(P);
+    tc_fp8_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(mapA, mapB, P);
     note_launch();
     return check_launch();
 }
