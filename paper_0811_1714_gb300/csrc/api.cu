@@ -261,9 +261,13 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
                         m, l, n, 1, accumulate, s);
 
-    // top-down: the 8 additions of Algorithm 4 for every sub-problem of each level
+    // top-down: the 8 additions of Algorithm 4 for every sub-problem of each
+    // level; two levels per launch while at least two remain (the middle
+    // level's operands then never leave registers)
     int64_t cnt = 1;
-    for (int j = 1; j <= d; ++j) {
+    for (int j = 1; j <= d;) {
+        const int step = (d - j + 1 >= 2) ? 2 : 1;
+        const int jt = j + step - 1;                       // level written
         const int64_t Mp = p.M >> (j - 1), Lp = p.L >> (j - 1), Np = p.N >> (j - 1);
         SplitLaunch SA;
         SA.nparent = (int)cnt;
@@ -275,9 +279,9 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
             SA.X = reinterpret_cast<const uint64_t *>(scratch + p.offA[j - 1]);
             SA.ld = p.ldA[j - 1]; SA.bs = p.slabA[j - 1]; SA.vrows = Mp; SA.vcols = Lp;
         }
-        SA.out = reinterpret_cast<uint64_t *>(scratch + p.offA[j]);
-        SA.cld = p.ldA[j]; SA.cbs = p.slabA[j];
-        int rc = sw_split_launch(SA, s);
+        SA.out = reinterpret_cast<uint64_t *>(scratch + p.offA[jt]);
+        SA.cld = p.ldA[jt]; SA.cbs = p.slabA[jt];
+        int rc = step == 2 ? sw_split2_launch(SA, s) : sw_split_launch(SA, s);
         if (rc) return rc;
 
         SplitLaunch SB;
@@ -301,11 +305,12 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
                 SB.ld = p.ldB[j - 1]; SB.bs = p.slabB[j - 1]; SB.vrows = Lp; SB.vcols = Np;
             }
         }
-        SB.out = reinterpret_cast<uint64_t *>(scratch + p.offB[j]);
-        SB.cld = p.ldB[j]; SB.cbs = p.slabB[j];
-        rc = sw_split_launch(SB, s);
+        SB.out = reinterpret_cast<uint64_t *>(scratch + p.offB[jt]);
+        SB.cld = p.ldB[jt]; SB.cbs = p.slabB[jt];
+        rc = step == 2 ? sw_split2_launch(SB, s) : sw_split_launch(SB, s);
         if (rc) return rc;
-        cnt *= 7;
+        cnt *= (step == 2) ? 49 : 7;
+        j += step;
     }
     // all 7^d leaf products in one launch of the base case
     {
@@ -316,24 +321,28 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
                           Nd, (int)cnt, 0, s);
         if (rc) return rc;
     }
-    // bottom-up: the 7 final additions of Algorithm 4, Augment and Stack
-    for (int j = d; j >= 1; --j) {
-        cnt /= 7;
-        const int64_t Mp = p.M >> (j - 1), Np = p.N >> (j - 1);
+    // bottom-up: the 7 final additions of Algorithm 4, Augment and Stack,
+    // two levels per launch while at least two remain
+    for (int j = d; j >= 1;) {
+        const int step = (j >= 2) ? 2 : 1;
+        const int jp = j - step;                           // level written (0 = C itself)
+        cnt /= (step == 2) ? 49 : 7;
+        const int64_t Mp = p.M >> jp, Np = p.N >> jp;
         CombineLaunch CL;
         CL.P = reinterpret_cast<const uint64_t *>(scratch + p.offP[j]);
         CL.pld = p.ldP[j]; CL.pbs = p.slabP[j];
         CL.rows = Mp; CL.cols = Np; CL.nparent = (int)cnt;
-        if (j == 1) {
+        if (jp == 0) {
             CL.X = C->data; CL.ld = C->stride_words; CL.bs = 0; CL.vrows = m; CL.vcols = n;
             CL.accumulate = accumulate;
         } else {
-            CL.X = reinterpret_cast<uint64_t *>(scratch + p.offP[j - 1]);
-            CL.ld = p.ldP[j - 1]; CL.bs = p.slabP[j - 1]; CL.vrows = Mp; CL.vcols = Np;
+            CL.X = reinterpret_cast<uint64_t *>(scratch + p.offP[jp]);
+            CL.ld = p.ldP[jp]; CL.bs = p.slabP[jp]; CL.vrows = Mp; CL.vcols = Np;
             CL.accumulate = 0;
         }
-        int rc = sw_combine_launch(CL, s);
+        int rc = step == 2 ? sw_combine2_launch(CL, s) : sw_combine_launch(CL, s);
         if (rc) return rc;
+        j -= step;
     }
     return GF2_OK;
 }

@@ -103,6 +103,12 @@ struct CombineLaunch {
 };
 int sw_combine_launch(const CombineLaunch &L, cudaStream_t s);
 
+// Two levels at once (rows divisible by 4, cols by 512): split writes the 49
+// grandchild operands (out, cld, cbs describe the grandchild slabs); combine
+// reads the 49 grandchild products (P, pld, pbs) and writes the parent.
+int sw_split2_launch(const SplitLaunch &L, cudaStream_t s);
+int sw_combine2_launch(const CombineLaunch &L, cudaStream_t s);
+
 // Utilities.
 int random_launch(DMat M, uint64_t seed, double p, cudaStream_t s);
 int transpose_launch(DMat T, DMat X, cudaStream_t s);

@@ -42,6 +42,47 @@ __device__ __forceinline__ uint4 ld_virtual(const uint64_t *X, int64_t ld, int64
     return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
 }
 
+// The 8 additions of Algorithm 4 for one position of the four quadrants:
+// the operands of P0..P6.  side 0: left factor A (S0..S3); side 1: right
+// factor B (T0..T3); side 2: B^T, whose NE quadrant is (B_SW)^T and SW is
+// (B_NE)^T (so the roles of NE and SW swap).
+__device__ __forceinline__ void split_one(int side, uint4 nw, uint4 ne, uint4 sw, uint4 se, uint4 (&o)[7])
+{
+    if (side == 0) {
+        // S0 = A_SW + A_SE, S1 = S0 + A_NW, S2 = A_NW + A_SW, S3 = A_NE + S1
+        const uint4 s0 = xr(sw, se);
+        const uint4 s1 = xr(s0, nw);
+        const uint4 s2 = xr(nw, sw);
+        const uint4 s3 = xr(ne, s1);
+        // left factors of P0..P6: A_NW, A_NE, S3, A_SE, S0, S1, S2
+        o[0] = nw; o[1] = ne; o[2] = s3; o[3] = se; o[4] = s0; o[5] = s1; o[6] = s2;
+    } else {
+        if (side == 2) { const uint4 tmp = ne; ne = sw; sw = tmp; }
+        // T0 = B_NE + B_NW, T1 = B_SE + T0, T2 = B_SE + B_NE, T3 = T1 + B_SW
+        const uint4 t0 = xr(ne, nw);
+        const uint4 t1 = xr(se, t0);
+        const uint4 t2 = xr(se, ne);
+        const uint4 t3 = xr(t1, sw);
+        // right factors of P0..P6: B_NW, B_SW, B_SE, T3, T0, T1, T2 (transposed
+        // for side 2, where B_SW^T is the NE quadrant swapped in above)
+        o[0] = nw; o[1] = sw; o[2] = se; o[3] = t3; o[4] = t0; o[5] = t1; o[6] = t2;
+    }
+}
+
+// The 7 final additions of Algorithm 4 for one position: q = the values of
+// the quadrants NW, NE, SW, SE of Stack(Augment(U0, U4), Augment(U5, U6)).
+__device__ __forceinline__ void combine_one(const uint4 (&p)[7], uint4 (&q)[4])
+{
+    const uint4 u0 = xr(p[0], p[1]);
+    const uint4 u1 = xr(p[0], p[5]);
+    const uint4 u2 = xr(u1, p[6]);
+    const uint4 u3 = xr(u1, p[4]);
+    const uint4 u4 = xr(u3, p[2]);
+    const uint4 u5 = xr(u2, p[3]);
+    const uint4 u6 = xr(u2, p[4]);
+    q[0] = u0; q[1] = u4; q[2] = u5; q[3] = u6;
+}
+
 template <bool TOP>
 __global__ void __launch_bounds__(256) sw_split_kernel(SplitLaunch L)
 {
@@ -70,26 +111,7 @@ __global__ void __launch_bounds__(256) sw_split_kernel(SplitLaunch L)
             se = ld4(X + (r + hr) * L.ld + w + hw);
         }
         uint4 o[7];
-        if (L.side == 0) {
-            // A side: S0 = A_SW + A_SE, S1 = S0 + A_NW, S2 = A_NW + A_SW, S3 = A_NE + S1
-            const uint4 s0 = xr(sw, se);
-            const uint4 s1 = xr(s0, nw);
-            const uint4 s2 = xr(nw, sw);
-            const uint4 s3 = xr(ne, s1);
-            // left factors of P0..P6: A_NW, A_NE, S3, A_SE, S0, S1, S2
-            o[0] = nw; o[1] = ne; o[2] = s3; o[3] = se; o[4] = s0; o[5] = s1; o[6] = s2;
-        } else {
-            // side 2: X is B^T, whose NE quadrant is (B_SW)^T and SW is (B_NE)^T
-            if (L.side == 2) { const uint4 tmp = ne; ne = sw; sw = tmp; }
-            // B side: T0 = B_NE + B_NW, T1 = B_SE + T0, T2 = B_SE + B_NE, T3 = T1 + B_SW
-            const uint4 t0 = xr(ne, nw);
-            const uint4 t1 = xr(se, t0);
-            const uint4 t2 = xr(se, ne);
-            const uint4 t3 = xr(t1, sw);
-            // right factors of P0..P6: B_NW, B_SW, B_SE, T3, T0, T1, T2 (transposed
-            // for side 2, where B_SW^T is the NE quadrant swapped in above)
-            o[0] = nw; o[1] = sw; o[2] = se; o[3] = t3; o[4] = t0; o[5] = t1; o[6] = t2;
-        }
+        split_one(L.side, nw, ne, sw, se, o);
         uint64_t *dst = L.out + (par * 7) * L.cbs + r * L.cld + w;
 #pragma unroll
         for (int j = 0; j < 7; ++j) st4(dst + j * L.cbs, o[j]);
@@ -115,14 +137,10 @@ __global__ void __launch_bounds__(256) sw_combine_kernel(CombineLaunch L)
         const uint4 p0 = ld4(Pp), p1 = ld4(Pp + L.pbs), p2 = ld4(Pp + 2 * L.pbs),
                     p3 = ld4(Pp + 3 * L.pbs), p4 = ld4(Pp + 4 * L.pbs), p5 = ld4(Pp + 5 * L.pbs),
                     p6 = ld4(Pp + 6 * L.pbs);
-        // the 7 final additions of Algorithm 4
-        const uint4 u0 = xr(p0, p1);
-        const uint4 u1 = xr(p0, p5);
-        const uint4 u2 = xr(u1, p6);
-        const uint4 u3 = xr(u1, p4);
-        const uint4 u4 = xr(u3, p2);
-        const uint4 u5 = xr(u2, p3);
-        const uint4 u6 = xr(u2, p4);
+        const uint4 pp[7] = {p0, p1, p2, p3, p4, p5, p6};
+        uint4 qv[4];
+        combine_one(pp, qv);
+        const uint4 u0 = qv[0], u4 = qv[1], u5 = qv[2], u6 = qv[3];
         // C = Stack(Augment(U0, U4), Augment(U5, U6))
         uint64_t *X = L.X + par * L.bs;
         const uint4 q[4] = {u0, u4, u5, u6};
@@ -150,6 +168,114 @@ __global__ void __launch_bounds__(256) sw_combine_kernel(CombineLaunch L)
     }
 }
 
+// Two levels of Algorithm 4 in one pass (the recursion applied to all 7
+// operands of a level without writing them out): each thread reads the 16
+// sub-blocks (q1 = quadrant, q2 = its quadrant) of one position of a parent
+// and writes the 49 operands of the grandchild products, product
+// 7 * (7 * parent + j1) + j2, the same order two single levels give.
+template <bool TOP>
+__global__ void __launch_bounds__(256) sw_split2_kernel(SplitLaunch L)
+{
+    const int64_t qr = L.rows / 4;            // grandchild rows
+    const int64_t qw = L.cols / 256;          // grandchild words per row (even)
+    const int64_t qq = qw / 2;
+    const int64_t hrw = L.rows / 2, hw = L.cols / 128;
+    const int64_t per_parent = qr * qq;
+    const int64_t total = per_parent * L.nparent;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t par = i / per_parent;
+        const int64_t rem = i - par * per_parent;
+        const int64_t r = rem / qq;
+        const int64_t w = (rem - r * qq) * 2;
+        const uint64_t *X = L.X + par * L.bs;
+        uint4 child[7][4];                    // level-1 operands at the 4 sub-positions
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+            uint4 v[4];
+#pragma unroll
+            for (int q1 = 0; q1 < 4; ++q1) {
+                const int64_t row = (q1 >> 1) * hrw + (q2 >> 1) * qr + r;
+                const int64_t wd = (q1 & 1) * hw + (q2 & 1) * qw + w;
+                v[q1] = TOP ? ld_virtual(X, L.ld, row, wd, L.vrows, L.vcols) : ld4(X + row * L.ld + wd);
+            }
+            uint4 o[7];
+            split_one(L.side, v[0], v[1], v[2], v[3], o);
+#pragma unroll
+            for (int j = 0; j < 7; ++j) child[j][q2] = o[j];
+        }
+        uint64_t *dst = L.out + (par * 49) * L.cbs + r * L.cld + w;
+#pragma unroll
+        for (int j1 = 0; j1 < 7; ++j1) {
+            uint4 g[7];
+            split_one(L.side, child[j1][0], child[j1][1], child[j1][2], child[j1][3], g);
+#pragma unroll
+            for (int j2 = 0; j2 < 7; ++j2) st4(dst + (j1 * 7 + j2) * L.cbs, g[j2]);
+        }
+    }
+}
+
+// Two levels of the final additions in one pass: reads the 49 grandchild
+// products of one position and writes the 16 sub-blocks of the parent.
+template <bool TOP>
+__global__ void __launch_bounds__(256) sw_combine2_kernel(CombineLaunch L)
+{
+    const int64_t qr = L.rows / 4;
+    const int64_t qw = L.cols / 256;
+    const int64_t qq = qw / 2;
+    const int64_t hrw = L.rows / 2, hw = L.cols / 128;
+    const int64_t per_parent = qr * qq;
+    const int64_t total = per_parent * L.nparent;
+    const int64_t vW = words_of(L.vcols);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t par = i / per_parent;
+        const int64_t rem = i - par * per_parent;
+        const int64_t r = rem / qq;
+        const int64_t w = (rem - r * qq) * 2;
+        const uint64_t *Pp = L.P + (par * 49) * L.pbs + r * L.pld + w;
+        uint4 cq[7][4];                       // quadrant values of the 7 level-1 products
+#pragma unroll
+        for (int j1 = 0; j1 < 7; ++j1) {
+            uint4 p[7];
+#pragma unroll
+            for (int j2 = 0; j2 < 7; ++j2) p[j2] = ld4(Pp + (j1 * 7 + j2) * L.pbs);
+            uint4 q[4];
+            combine_one(p, q);
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) cq[j1][q2] = q[q2];
+        }
+        uint64_t *X = L.X + par * L.bs;
+#pragma unroll
+        for (int q2 = 0; q2 < 4; ++q2) {
+            const uint4 p[7] = {cq[0][q2], cq[1][q2], cq[2][q2], cq[3][q2], cq[4][q2], cq[5][q2], cq[6][q2]};
+            uint4 out[4];
+            combine_one(p, out);
+#pragma unroll
+            for (int q1 = 0; q1 < 4; ++q1) {
+                const int64_t row = (q1 >> 1) * hrw + (q2 >> 1) * qr + r;
+                const int64_t wd = (q1 & 1) * hw + (q2 & 1) * qw + w;
+                uint64_t *d = X + row * L.ld + wd;
+                if (TOP) {
+                    if (row >= L.vrows) continue;
+                    const uint64_t a = ((uint64_t)out[q1].y << 32) | out[q1].x;
+                    const uint64_t b = ((uint64_t)out[q1].w << 32) | out[q1].z;
+                    if (wd < vW) {
+                        const uint64_t v = a & word_mask(wd, L.vcols);
+                        d[0] = L.accumulate ? (d[0] ^ v) : v;
+                    }
+                    if (wd + 1 < vW) {
+                        const uint64_t v = b & word_mask(wd + 1, L.vcols);
+                        d[1] = L.accumulate ? (d[1] ^ v) : v;
+                    }
+                } else {
+                    st4(d, L.accumulate ? xr(*reinterpret_cast<const uint4 *>(d), out[q1]) : out[q1]);
+                }
+            }
+        }
+    }
+}
+
 int grid_for(int64_t total)
 {
     int64_t b = (total + 255) / 256;
@@ -172,6 +298,36 @@ int sw_split_launch(const SplitLaunch &L, cudaStream_t s)
         sw_split_kernel<true><<<grid_for(total), 256, 0, s>>>(L);
     else
         sw_split_kernel<false><<<grid_for(total), 256, 0, s>>>(L);
+    note_launch();
+    return check_launch();
+}
+
+int sw_split2_launch(const SplitLaunch &L, cudaStream_t s)
+{
+    const int64_t total = (L.rows / 4) * (L.cols / 512) * L.nparent;
+    if (total <= 0) return GF2_OK;
+    const bool top = (L.vrows != L.rows) || (L.vcols != L.cols) || (L.ld & 1) ||
+                     (reinterpret_cast<uintptr_t>(L.X) & 15);
+    ProfScope ps(PF_SPLIT, s);
+    if (top)
+        sw_split2_kernel<true><<<grid_for(total), 256, 0, s>>>(L);
+    else
+        sw_split2_kernel<false><<<grid_for(total), 256, 0, s>>>(L);
+    note_launch();
+    return check_launch();
+}
+
+int sw_combine2_launch(const CombineLaunch &L, cudaStream_t s)
+{
+    const int64_t total = (L.rows / 4) * (L.cols / 512) * L.nparent;
+    if (total <= 0) return GF2_OK;
+    const bool top = (L.vrows != L.rows) || (L.vcols != L.cols) || (L.ld & 1) ||
+                     (reinterpret_cast<uintptr_t>(L.X) & 15);
+    ProfScope ps(PF_COMBINE, s);
+    if (top)
+        sw_combine2_kernel<true><<<grid_for(total), 256, 0, s>>>(L);
+    else
+        sw_combine2_kernel<false><<<grid_for(total), 256, 0, s>>>(L);
     note_launch();
     return check_launch();
 }
