@@ -29,6 +29,33 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "effective GF(2) bit-ops/s (2mnk/t) at n=32768, bit-exact"
+
+# DRAM traffic of the dominant kernel from an ncu capture of it (see
+# profiles/m4rm_kernel_n16384_depth2.md): bytes read + written per byte of leaf
+# operands (A, B, C slabs), valid while the kernel sources hash to "sha".
+NCU_TRAFFIC = {
+    "m4rm": {"sha": "edc62a0c0f6486c9", "sources": ["paper_0811_1714_gb300/csrc/m4rm.cu",
+                                         "paper_0811_1714_gb300/csrc/m4rm_dev.cuh"],
+             "bytes_per_operand_byte": 0.9099},
+}
+
+
+def ncu_traffic(fam, leaves, M, L, N):
+    """Per-launch DRAM bytes scaled from the capture, or None if the kernel changed."""
+    import hashlib
+    ent = NCU_TRAFFIC.get(fam)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    try:
+        for f in ent["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    if h.hexdigest()[:16] != ent["sha"]:
+        return None
+    return ent["bytes_per_operand_byte"] * leaves * (M * L + L * N + M * N) / 8.0
 UNIT = "bit-ops/s"
 
 
@@ -60,6 +87,25 @@ def load_peaks():
     except OSError:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------- ranks
+
+def aggregate(ms_local, ops_local):
+    """Whole-job timing over the ranks of the default process group: the
+    slowest rank's time, and the bit operations of all ranks over it.
+    Returns (ms, ops_total, value).  One process (no group): the local ones."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return ms_local, ops_local, ops_local / (ms_local * 1e-3)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=dev)
+    o = torch.tensor([float(ops_local)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(o, op=dist.ReduceOp.SUM)
+    ms, ops = float(t.item()), float(o.item())
+    return ms, ops, ops / (ms * 1e-3)
 
 
 # ---------------------------------------------------------------- clocks
@@ -137,7 +183,8 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
     achieved = smem_bytes / (ms_per_launch * 1e-3) / 1e9
     peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
     return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": ncu_traffic("m4rm", leaves, M, L, N),
+            "traffic_note": "DRAM bytes per launch, scaled by leaf operand bytes from a 49-leaf ncu capture",
             "peak_note": "152 SMs x 128 B/clk x %.0f MHz (shared-memory bandwidth)" %
                          peaks.get("sm_max_mhz", 2070.0)}
 
@@ -201,11 +248,7 @@ def run_ours(args, rank, world, local_rank):
             if c:
                 fam[name] = {"ms": t, "launches": c}
         g.gf2_profile_enable(False)
-        if dist is not None:
-            tt = torch.tensor([ms_total], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_total = float(tt.item())
-        ms = ms_total / args.steps
+        ms, _, value = aggregate(ms_total / args.steps, 2.0 * m * l * n)
         bad = g.gf2_freivalds(MC, MA, MB, 1000 + rank)
         # plan fields
         kv = dict(x.split("=", 1) for x in plan.split() if "=" in x)
@@ -218,7 +261,7 @@ def run_ours(args, rank, world, local_rank):
         rl = roofline_for(dom, leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
             if dom in ("m4rm", "tc_fp8") else None
         results[path] = {
-            "ms": ms, "value": 2.0 * m * l * n * world / (ms * 1e-3), "depth": d, "plan": plan,
+            "ms": ms, "value": value, "depth": d, "plan": plan,
             "gpu_launches": launches, "kernels": fam, "dominant": dom,
             "dominant_ms_per_launch": dom_ms, "roofline": rl,
             "freivalds_mismatched_rows": bad, "clocks": cs.summary(),
@@ -246,13 +289,10 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.steps):
             g.gf2_mul(hMC, hMA, hMB, o)         # returns after the D2H copy completed
         t_e2e = (time.perf_counter() - t0) / args.steps
-        if dist is not None:
-            tt = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        ms_e2e, _, v_e2e = aggregate(t_e2e * 1e3, 2.0 * m * l * n)
         same = bool(torch.equal(hC.cuda(), C))
-        e2e = {"value": 2.0 * m * l * n * world / t_e2e, "unit": UNIT,
-               "ms_per_step": t_e2e * 1e3,
+        e2e = {"value": v_e2e, "unit": UNIT,
+               "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": (hA.numel() + hB.numel()) * 8,
                "d2h_bytes_per_step": hC.numel() * 8, "matches_device_result": same}
 
@@ -364,12 +404,12 @@ def run_batched(args, rank, world, local_rank):
         g.gf2_mul_batched(arrs)
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms, ops, value = aggregate(ev0.elapsed_time(ev1) / args.steps, ops)
     launches = g.gf2_launch_count() - launches0
     g.gf2_profile_enable(False)
     bad = sum(1 for i in range(0, len(dims), 64) if g.gf2_freivalds(MC[i], MA[i], MB[i], 5 + i))
     return {
-        "metric": "effective GF(2) bit-ops/s (2mnk/t), 4096 batched products", "value": ops / (ms * 1e-3),
+        "metric": "effective GF(2) bit-ops/s (2mnk/t), 4096 batched products", "value": value,
         "unit": "bit-ops/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64-packed-bits", "data": "synthetic: SplitMix64 bits, dims log-uniform [64, 2048] seed 42",
@@ -416,8 +456,9 @@ def run_chain(args, rank, world, local_rank):
     t2 /= args.steps
     ops1, ops2 = 2.0 * M * K1 * N1, 2.0 * M * N1 * N2
     ok = (g.gf2_freivalds(MAB, MA, MB, 1000) == 0) and (g.gf2_freivalds(MABC, MAB, MC, 1001) == 0)
+    _, _, value = aggregate(t1 + t2, ops1 + ops2)
     return {
-        "metric": "effective GF(2) bit-ops/s (2mnk/t), chain A.B then .C", "value": (ops1 + ops2) / ((t1 + t2) * 1e-3),
+        "metric": "effective GF(2) bit-ops/s (2mnk/t), chain A.B then .C", "value": value,
         "unit": "bit-ops/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t1 + t2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "auto", "data": "synthetic: SplitMix64 Bernoulli(1/2) bits, seeds 31/32/33",

@@ -224,6 +224,15 @@ int64_t gf2_launch_count(void);
  */
 int gf2_device_status(void *cuda_stream);
 
+/* gf2_selftest_wait: tests the failure detection without a GPU fault.
+ * Launches one CTA whose single wait can never be satisfied (an mbarrier no
+ * one arrives on); after `limit_cycles` SM clock cycles (1 .. 4e9) the wait
+ * gives up and records GF2_ETIMEOUT in the same status word the tensor-core
+ * kernels use, so the next gf2_device_status returns GF2_ETIMEOUT and the
+ * context stays usable.
+ */
+int gf2_selftest_wait(int64_t limit_cycles, void *cuda_stream);
+
 /* ---- device-time accounting ----------------------------------------------
  * gf2_profile_enable(1) clears the counters and starts bracketing every
  * kernel launch of the library with CUDA events on its stream; (0) stops.

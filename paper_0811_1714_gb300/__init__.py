@@ -52,7 +52,7 @@ EXPORTS = (
     "gf2_freivalds", "gf2_scratch_bytes", "gf2_reserve_scratch", "gf2_release_scratch",
     "gf2_launch_count", "gf2_describe_plan", "gf2_profile_enable", "gf2_profile_read",
     "gf2_profile_name", "gf2_mul_noalloc", "gf2_device_status", "gf2_mul_batched_ex",
-    "gf2_batched_variant_count", "gf2_batched_variant_name",
+    "gf2_batched_variant_count", "gf2_batched_variant_name", "gf2_selftest_wait",
 )
 
 
@@ -140,6 +140,7 @@ def lib():
                                                       _P(Opts), i32, _P(i32), vp]),
                 "gf2_batched_variant_count": (i32, []),
                 "gf2_batched_variant_name": (ctypes.c_char_p, [i32]),
+                "gf2_selftest_wait": (ctypes.c_int, [i64, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -343,6 +344,11 @@ def gf2_strerror(status: int) -> str:
 def gf2_device_status(stream=None) -> None:
     """Raise GF2Error(GF2_ETIMEOUT) when a bounded device wait expired."""
     _check(lib().gf2_device_status(_stream(stream)), "gf2_device_status")
+
+
+def gf2_selftest_wait(limit_cycles: int, stream=None) -> None:
+    """Launch a wait that can only time out (failure-detection self test)."""
+    _check(lib().gf2_selftest_wait(limit_cycles, _stream(stream)), "gf2_selftest_wait")
 
 
 def gf2_profile_enable(on: bool) -> None:

@@ -587,6 +587,12 @@ int64_t gf2_launch_count(void) { return (int64_t)gf2::launch_count(); }
 
 int gf2_profile_enable(int32_t on) { return gf2::profile_enable(on); }
 
+int gf2_selftest_wait(int64_t limit_cycles, void *stream)
+{
+    if (limit_cycles < 1 || limit_cycles > 4000000000ll) return GF2_EINVAL;
+    return gf2::wait_selftest_launch(limit_cycles, static_cast<cudaStream_t>(stream));
+}
+
 int gf2_device_status(void *stream)
 {
     unsigned int v = 0;

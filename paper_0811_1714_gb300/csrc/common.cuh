@@ -144,6 +144,7 @@ int batched_variant_count();
 const char *batched_variant_name(int i);
 void batched_release();
 int tc_status_read_and_clear(unsigned int *out, cudaStream_t s);
+int wait_selftest_launch(long long limit, cudaStream_t s);
 bool tc_fp8_available();
 
 }  // namespace gf2

@@ -474,6 +474,28 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
 __device__ unsigned int g_tc_status;   // -GF2_ETIMEOUT after an expired wait
 
+// Failure-detection self test: one wait that nothing can satisfy (an mbarrier
+// nobody arrives on), bounded by `limit` clock cycles; it records
+// GF2_ETIMEOUT in the status word exactly like the product kernels do.
+__global__ void wait_selftest_kernel(unsigned long long limit, unsigned int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        while (!mbar_try_wait(smem_u32(&bar), 0)) {
+            if ((unsigned long long)(clock64() - t0) > limit) {
+                atomicExch(status, (unsigned int)(-GF2_ETIMEOUT));
+                break;
+            }
+        }
+    }
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once (no link-time
 // dependency on the driver library).
 using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -527,6 +549,15 @@ bool tc_fp8_available()
         return false;
     }
     return major == 10 && minor == 3 && encode_fn() != nullptr;     // built for sm_103a only
+}
+
+int wait_selftest_launch(long long limit, cudaStream_t s)
+{
+    unsigned int *st = nullptr;
+    GF2_CUDA_TRY(cudaGetSymbolAddress((void **)&st, g_tc_status));
+    wait_selftest_kernel<<<1, 32, 0, s>>>((unsigned long long)limit, st);
+    note_launch();
+    return check_launch();
 }
 
 int tc_status_read_and_clear(unsigned int *out, cudaStream_t s)
