@@ -51,9 +51,10 @@ struct BTile {
 
 template <int KB, int NT, int LPR, int R, int NW>
 __global__ void __launch_bounds__(NW * 32) m4rm_batched_kernel(const BProd *__restrict__ prods,
-                                                               const BTile *__restrict__ tiles, int ntiles,
+                                                               const void *__restrict__ tiles_v, int ntiles,
                                                                unsigned int *counter, int accumulate)
 {
+    const BTile *tiles = static_cast<const BTile *>(tiles_v);
     constexpr int NTH = NW * 32;
     constexpr int KG = KB * NT;
     constexpr int TROWS = 1 << KB;
@@ -188,13 +189,171 @@ __global__ void __launch_bounds__(NW * 32) m4rm_batched_kernel(const BProd *__re
     }
 }
 
-using BatchedFn = void (*)(const BProd *, const BTile *, int, unsigned int *, int);
+// Slot-packed tiles: a 1024-column tile whose 8 column chunks (128 columns,
+// one per lane of a quarter-warp) come from up to 8 different products.  A
+// slot is (product, first row, first word) of a BM x 128 block of that
+// product's C; each lane works on its own slot's A rows, B rows and masks,
+// so narrow products fill whole tiles.  Table reads stay one full 128-byte
+// row per quarter-warp (conflict free).
+struct PSlot {
+    int prod;     // -1: empty slot
+    int row0;
+    int word0;
+    int pad;
+};
+struct PTile {
+    PSlot slot[8];
+    int groups;   // passes: the largest of the slots' ceil(l / (k t))
+    int pad[3];
+};
+
+template <int KB, int NT, int R, int NW>
+__global__ void __launch_bounds__(NW * 32) m4rm_slots_kernel(const BProd *__restrict__ prods,
+                                                             const void *__restrict__ tiles_v, int ntiles,
+                                                             unsigned int *counter, int accumulate)
+{
+    constexpr int LPR = 8;
+    constexpr int NTH = NW * 32;
+    constexpr int KG = KB * NT;
+    constexpr int TROWS = 1 << KB;
+    constexpr int BM = NW * 4 * R;
+    constexpr int PPC = 128 / KG;                         // passes per staged A chunk
+    constexpr unsigned IMASK = (1u << KB) - 1u;
+    static_assert(128 % KG == 0, "slot tiles stage A in 128-column chunks");
+    const PTile *tiles = static_cast<const PTile *>(tiles_v);
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);   // NT * TROWS * 8
+    uint4 *stg = tab + NT * TROWS * LPR;                  // 2 * KG * 8
+    uint4 *sta = stg + 2 * KG * LPR;                      // 2 * BM * 8: A chunk of (row, slot)
+    __shared__ BProd sp[8];
+    __shared__ PSlot ss[8];
+    __shared__ int s_tile;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int c = lane & 7;                               // my slot
+    const int trow = warp * 4 * R + (lane >> 3);
+
+    while (true) {
+        if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        if (tid < 8) {
+            const PSlot sl = tiles[t].slot[tid];
+            ss[tid] = sl;
+            if (sl.prod >= 0) sp[tid] = prods[sl.prod];
+        }
+        const int groups = tiles[t].groups;
+        __syncthreads();
+        const bool mine = ss[c].prod >= 0;
+        const int64_t my_m = mine ? sp[c].m : 0, my_l = mine ? sp[c].l : 0, my_n = mine ? sp[c].n : 0;
+        const int64_t my_row0 = ss[c].row0, my_w = ss[c].word0;
+        const uint64_t cm0 = mine ? word_mask(my_w, my_n) : 0ull, cm1 = mine ? word_mask(my_w + 1, my_n) : 0ull;
+        const uint4 cmask = make_uint4((uint32_t)cm0, (uint32_t)(cm0 >> 32), (uint32_t)cm1, (uint32_t)(cm1 >> 32));
+        uint4 acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+
+        auto issue_stage = [&](int g, int buf, bool a_chunk) {
+#pragma unroll 1
+            for (int i = tid; i < KG * LPR; i += NTH) {
+                const int rr = i >> 3, cc = i & 7;
+                const int64_t brow = (int64_t)g * KG + rr;
+                const bool valid = ss[cc].prod >= 0 && brow < sp[cc].l && ss[cc].word0 < words_of(sp[cc].n);
+                const uint64_t *src = valid ? (sp[cc].B + brow * sp[cc].ldb + ss[cc].word0) : prods[0].B;
+                cp_async16(&stg[buf * KG * LPR + i], src, valid);
+            }
+            if (a_chunk) {
+                const int64_t wa = 2 * (int64_t)(g / PPC);
+                const int abuf = (g / PPC) & 1;
+#pragma unroll 1
+                for (int i = tid; i < BM * LPR; i += NTH) {
+                    const int row = i >> 3, cc = i & 7;
+                    const int64_t grow = (int64_t)ss[cc].row0 + row;
+                    const bool valid = ss[cc].prod >= 0 && grow < sp[cc].m && wa < words_of(sp[cc].l);
+                    const uint64_t *src = valid ? (sp[cc].A + grow * sp[cc].lda + wa) : prods[0].A;
+                    cp_async16(&sta[abuf * BM * LPR + i], src, valid);
+                }
+            }
+            cp_async_commit();
+        };
+
+        if (groups > 0) issue_stage(0, 0, true);
+#pragma unroll 1
+        for (int g = 0; g < groups; ++g) {
+            const int buf = g & 1;
+            cp_async_wait_all();
+            __syncthreads();
+            if (g + 1 < groups) issue_stage(g + 1, buf ^ 1, ((g + 1) % PPC) == 0);
+            build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
+            __syncthreads();
+            const int64_t kb = (int64_t)g * KG;
+            const int64_t wa = kb >> 6;
+            const int sh = (int)(kb & 63);
+            const uint64_t mlo = mine ? word_mask(wa, my_l) : 0ull;
+            const uint4 *arow = sta + ((g / PPC) & 1) * BM * LPR + trow * LPR + c;
+            const int aoff = (int)(wa & 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint2 aw = reinterpret_cast<const uint2 *>(&arow[4 * r * LPR])[aoff];
+                const uint64_t bits = ((((uint64_t)aw.y << 32) | aw.x) & mlo) >> sh;
+                uint4 a = acc[r];
+#pragma unroll
+                for (int ti = 0; ti < NT; ++ti) {
+                    const unsigned x = (unsigned)(bits >> (ti * KB)) & IMASK;
+                    a = x4(a, tab[(ti * TROWS + (int)x) * LPR + c]);
+                }
+                acc[r] = a;
+                asm volatile("" ::: "memory");
+            }
+        }
+
+        const int64_t nW = words_of(my_n);
+        if (mine && my_w < nW) {
+            const int64_t first = my_row0 + trow;
+            const int64_t left = my_m - first;
+            const int nrows = left <= 0 ? 0 : (left < 4 * R ? (int)left : 4 * R);
+            uint64_t *cr = sp[c].C + first * sp[c].ldc + my_w;
+            const int64_t step = 4 * sp[c].ldc;
+            const bool two = my_w + 1 < nW;
+            if (!accumulate && two) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (4 * r < nrows) *reinterpret_cast<uint4 *>(cr + r * step) = and4(acc[r], cmask);
+            } else {
+#pragma unroll 1
+                for (int r = 0; r < R; ++r) {
+                    if (4 * r >= nrows) break;
+                    uint4 a = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+                        if (q == r) a = acc[q];
+                    const uint64_t v0 = ((uint64_t)a.y << 32 | a.x) & cm0;
+                    const uint64_t v1 = ((uint64_t)a.w << 32 | a.z) & cm1;
+                    uint64_t *cc = cr + r * step;
+                    if (accumulate) {
+                        cc[0] ^= v0;
+                        if (two) cc[1] ^= v1;
+                    } else {
+                        cc[0] = v0;
+                    }
+                }
+            }
+        }
+        __syncthreads();    // s_tile, slot descriptors and shared buffers are reused
+    }
+}
+
+using BatchedFn = void (*)(const BProd *, const void *, int, unsigned int *, int);
 
 struct BVariant {
     const char *name;
     int k, t, lpr, bm, nw;
     BatchedFn fn;
     int smem;
+    int packed;   // 1: slot-packed tiles (PTile), 0: one product per tile (BTile)
 };
 
 template <int KB, int NT, int LPR, int R, int NW>
@@ -202,7 +361,15 @@ BVariant make_bvariant(const char *name)
 {
     constexpr int BM = NW * (32 / LPR) * R;
     return BVariant{name, KB, NT, LPR, BM, NW, &m4rm_batched_kernel<KB, NT, LPR, R, NW>,
-                    NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16};
+                    NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16, 0};
+}
+
+template <int KB, int NT, int R, int NW>
+BVariant make_slot_variant(const char *name)
+{
+    constexpr int BM = NW * 4 * R;
+    return BVariant{name, KB, NT, 8, BM, NW, &m4rm_slots_kernel<KB, NT, R, NW>,
+                    NT * (1 << KB) * 8 * 16 + 2 * KB * NT * 8 * 16 + 2 * BM * 8 * 16, 1};
 }
 
 const std::vector<BVariant> &bvariants()
@@ -216,33 +383,73 @@ const std::vector<BVariant> &bvariants()
         make_bvariant<6, 8, 2, 4, 8>("k6t8-w256-bm512"),
         make_bvariant<4, 8, 2, 2, 8>("k4t8-w256-bm256"),
         make_bvariant<8, 4, 4, 16, 8>("k8t4-w512-bm1024"),
+        make_slot_variant<8, 4, 8, 8>("slots-k8t4-bm256"),
+        make_slot_variant<4, 8, 8, 8>("slots-k4t8-bm256"),
+        make_slot_variant<4, 8, 4, 8>("slots-k4t8-bm128"),
     };
     return v;
 }
 
 // ------------------------------------------------------------------ planning
 
-struct Built {
-    int variant = -1;
-    std::vector<BProd> prods;
-    std::vector<BTile> tiles;
-};
-
-void build_tiles(const std::vector<BProd> &prods, const BVariant &v, std::vector<BTile> &tiles)
+// Tile descriptors of a variant, as bytes (BTile or PTile records).
+void build_tiles(const std::vector<BProd> &prods, const BVariant &v, std::vector<unsigned char> &bytes, int *ntiles)
 {
-    tiles.clear();
-    const int tw = 2 * v.lpr;
+    bytes.clear();
+    *ntiles = 0;
+    if (!v.packed) {
+        std::vector<BTile> tiles;
+        const int tw = 2 * v.lpr;
+        for (size_t i = 0; i < prods.size(); ++i) {
+            const BProd &p = prods[i];
+            if (p.m <= 0 || p.n <= 0) continue;
+            const int64_t W = words_of(p.n);
+            for (int64_t r = 0; r < p.m; r += v.bm)
+                for (int64_t w = 0; w < W; w += tw) tiles.push_back(BTile{(int)i, (int)r, (int)w, 0});
+        }
+        // longest K first (the work of a tile grows with the K extent)
+        std::stable_sort(tiles.begin(), tiles.end(), [&](const BTile &a, const BTile &b) {
+            return prods[a.prod].l > prods[b.prod].l;
+        });
+        bytes.resize(tiles.size() * sizeof(BTile));
+        if (!tiles.empty()) memcpy(bytes.data(), tiles.data(), bytes.size());
+        *ntiles = (int)tiles.size();
+        return;
+    }
+    // slot units: (product, row block, 128-column chunk), grouped 8 per tile
+    // among units with similar pass counts and row counts
+    struct Unit { int prod, row0, word0, groups, rows; };
+    std::vector<Unit> units;
+    const int kg = v.k * v.t;
     for (size_t i = 0; i < prods.size(); ++i) {
         const BProd &p = prods[i];
         if (p.m <= 0 || p.n <= 0) continue;
         const int64_t W = words_of(p.n);
+        const int groups = (int)((p.l + kg - 1) / kg);
         for (int64_t r = 0; r < p.m; r += v.bm)
-            for (int64_t w = 0; w < W; w += tw) tiles.push_back(BTile{(int)i, (int)r, (int)w, 0});
+            for (int64_t w = 0; w < W; w += 2)
+                units.push_back(Unit{(int)i, (int)r, (int)w, groups, (int)std::min<int64_t>(v.bm, p.m - r)});
     }
-    // longest K first (the work of a tile grows with the K extent)
-    std::stable_sort(tiles.begin(), tiles.end(), [&](const BTile &a, const BTile &b) {
-        return prods[a.prod].l > prods[b.prod].l;
+    std::stable_sort(units.begin(), units.end(), [](const Unit &a, const Unit &b) {
+        return a.groups != b.groups ? a.groups > b.groups : a.rows > b.rows;
     });
+    std::vector<PTile> tiles((units.size() + 7) / 8);
+    for (size_t t = 0; t < tiles.size(); ++t) {
+        PTile &T = tiles[t];
+        memset(&T, 0, sizeof T);
+        for (int j = 0; j < 8; ++j) {
+            const size_t u = t * 8 + j;
+            if (u < units.size()) {
+                T.slot[j] = PSlot{units[u].prod, units[u].row0, units[u].word0, 0};
+                T.groups = std::max(T.groups, units[u].groups);
+            } else {
+                T.slot[j] = PSlot{-1, 0, 0, 0};
+            }
+        }
+    }
+    bytes.resize(tiles.size() * sizeof(PTile));
+    if (!tiles.empty()) memcpy(bytes.data(), tiles.data(), bytes.size());
+    *ntiles = (int)tiles.size();
 }
 
 int grid_for(const BVariant &v)
@@ -299,11 +506,11 @@ void free_entry(GraphEntry &e)
 }
 
 // Device copies of the tables: [prods][tiles][counter]
-int upload(const std::vector<BProd> &prods, const std::vector<BTile> &tiles, void **dev, BProd **dp,
-           BTile **dt, unsigned int **dc)
+int upload(const std::vector<BProd> &prods, const std::vector<unsigned char> &tiles, void **dev, BProd **dp,
+           void **dt, unsigned int **dc)
 {
     const size_t bp = (prods.size() * sizeof(BProd) + 255) & ~(size_t)255;
-    const size_t bt = (tiles.size() * sizeof(BTile) + 255) & ~(size_t)255;
+    const size_t bt = (tiles.size() + 255) & ~(size_t)255;
     void *p = nullptr;
     if (cudaMalloc(&p, bp + bt + 256) != cudaSuccess) {
         cudaGetLastError();
@@ -312,15 +519,15 @@ int upload(const std::vector<BProd> &prods, const std::vector<BTile> &tiles, voi
     char *c = static_cast<char *>(p);
     GF2_CUDA_TRY(cudaMemcpy(c, prods.data(), prods.size() * sizeof(BProd), cudaMemcpyHostToDevice));
     if (!tiles.empty())
-        GF2_CUDA_TRY(cudaMemcpy(c + bp, tiles.data(), tiles.size() * sizeof(BTile), cudaMemcpyHostToDevice));
+        GF2_CUDA_TRY(cudaMemcpy(c + bp, tiles.data(), tiles.size(), cudaMemcpyHostToDevice));
     *dev = p;
     *dp = reinterpret_cast<BProd *>(c);
-    *dt = reinterpret_cast<BTile *>(c + bp);
+    *dt = c + bp;
     *dc = reinterpret_cast<unsigned int *>(c + bp + bt);
     return GF2_OK;
 }
 
-int launch_variant(const BVariant &v, const BProd *dp, const BTile *dt, int ntiles, unsigned int *dc,
+int launch_variant(const BVariant &v, const BProd *dp, const void *dt, int ntiles, unsigned int *dc,
                    int accumulate, cudaStream_t s)
 {
     GF2_CUDA_TRY(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
@@ -342,18 +549,19 @@ int autotune(const std::vector<BProd> &prods, int accumulate, cudaStream_t s)
     GF2_CUDA_TRY(cudaEventCreate(&e0));
     GF2_CUDA_TRY(cudaEventCreate(&e1));
     for (size_t i = 0; i < vs.size(); ++i) {
-        std::vector<BTile> tiles;
-        build_tiles(prods, vs[i], tiles);
+        std::vector<unsigned char> tiles;
+        int nt = 0;
+        build_tiles(prods, vs[i], tiles, &nt);
         void *dev = nullptr;
         BProd *dp;
-        BTile *dt;
+        void *dt;
         unsigned int *dc;
         if (upload(prods, tiles, &dev, &dp, &dt, &dc)) continue;
         float ms = 1e30f;
-        bool ok = launch_variant(vs[i], dp, dt, (int)tiles.size(), dc, accumulate, s) == GF2_OK;
+        bool ok = launch_variant(vs[i], dp, dt, nt, dc, accumulate, s) == GF2_OK;
         for (int rep = 0; ok && rep < 2; ++rep) {
             cudaEventRecord(e0, s);
-            ok = launch_variant(vs[i], dp, dt, (int)tiles.size(), dc, accumulate, s) == GF2_OK;
+            ok = launch_variant(vs[i], dp, dt, nt, dc, accumulate, s) == GF2_OK;
             cudaEventRecord(e1, s);
             float t = 0.f;
             if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
@@ -442,12 +650,13 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
     GraphEntry e;
     e.key = key;
     e.variant = vi;
-    std::vector<BTile> tiles;
-    build_tiles(prods, v, tiles);
-    e.ntiles = (int)tiles.size();
+    std::vector<unsigned char> tiles;
+    int nt_built = 0;
+    build_tiles(prods, v, tiles, &nt_built);
+    e.ntiles = nt_built;
     if (e.ntiles > 0) {
         BProd *dp;
-        BTile *dt;
+        void *dt;
         unsigned int *dc;
         int rc = upload(prods, tiles, &e.dev, &dp, &dt, &dc);
         if (rc) return rc;

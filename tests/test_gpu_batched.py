@@ -51,9 +51,12 @@ RAGGED = [(1, 1, 1), (64, 64, 64), (65, 63, 129), (300, 700, 100), (1000, 90, 10
           (17, 2048, 5), (513, 257, 511), (2048, 300, 2048), (129, 1, 300), (7, 4000, 260)]
 
 
-@pytest.mark.parametrize("variant", list(range(8)))
+NVARIANTS = 11   # 8 one-product-per-tile variants + 3 slot-packed variants
+
+
+@pytest.mark.parametrize("variant", list(range(NVARIANTS)))
 def test_every_batched_variant(variant):
-    assert g.gf2_batched_variant_count() == 8
+    assert g.gf2_batched_variant_count() == NVARIANTS
     bt = make_batch(RAGGED, 500)
     used = g.gf2_mul_batched_ex(bt["arrs"], variant=variant)
     assert used == variant
