@@ -392,22 +392,37 @@ def run_batched(args, rank, world, local_rank):
     arrs = g.MatArrays(MC, MA, MB)
     ops = sum(2.0 * m * l * n for m, l, n in dims)
     variant = g.gf2_mul_batched_ex(arrs)          # first call: autotune + graph build
-    for _ in range(args.warmup):
-        g.gf2_mul_batched(arrs)
     stream = torch.cuda.current_stream()
-    launches0 = g.gf2_launch_count()
+
+    def timed(options):
+        for _ in range(args.warmup):
+            g.gf2_mul_batched(arrs, options=options)
+        launches0 = g.gf2_launch_count()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            g.gf2_mul_batched(arrs, options=options)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / args.steps, g.gf2_launch_count() - launches0
+
+    def sampled_bad(seed0):
+        return sum(1 for i in range(0, len(dims), 64) if g.gf2_freivalds(MC[i], MA[i], MB[i], seed0 + i))
+
     g.gf2_profile_enable(True)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        g.gf2_mul_batched(arrs)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms, ops, value = aggregate(ev0.elapsed_time(ev1) / args.steps, ops)
-    launches = g.gf2_launch_count() - launches0
+    ms_local, launches = timed(None)
     g.gf2_profile_enable(False)
-    bad = sum(1 for i in range(0, len(dims), 64) if g.gf2_freivalds(MC[i], MA[i], MB[i], 5 + i))
+    bad = sampled_bad(5)
+    ms, ops_all, value = aggregate(ms_local, ops)
+    # the same batch on the tensor-core base case: one batched transpose and
+    # one persistent tensor-core launch per step
+    tc_ms_local, tc_launches = timed(g.opts(base=g.GF2_BASE_TC_FP8, depth=0))
+    tc_ms, _, tc_value = aggregate(tc_ms_local, ops)
+    tc = {"ms_per_step": tc_ms, "value": tc_value, "gpu_launches": tc_launches,
+          "graph": "batched transpose of every B + one persistent tensor-core kernel",
+          "freivalds_sampled_products_failed": sampled_bad(9)}
+    ops = ops_all
     return {
         "metric": "effective GF(2) bit-ops/s (2mnk/t), 4096 batched products", "value": value,
         "unit": "bit-ops/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -418,6 +433,7 @@ def run_batched(args, rank, world, local_rank):
         "gpu_launches": launches,
         "graph": "each step replays one CUDA graph: counter reset + one persistent kernel",
         "verified": {"freivalds_sampled_products_failed": bad},
+        "tc_fp8_base": tc,
     }
 
 

@@ -570,6 +570,7 @@ int gf2_release_scratch(void)
     int dev = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));
     gf2::batched_release();
+    gf2::tc_batched_release();
     std::lock_guard<std::mutex> lk(g_arena_mu);
     GF2_CUDA_TRY(cudaDeviceSynchronize());
     for (auto it = g_arenas.begin(); it != g_arenas.end();) {
@@ -745,8 +746,8 @@ int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[], const gf2_m
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // products for the single persistent launch, and the rest (recursing or
     // tensor-core plans) run one by one
-    std::vector<gf2_mat *> bc;
-    std::vector<const gf2_mat *> ba, bb;
+    std::vector<gf2_mat *> bc, tcc;
+    std::vector<const gf2_mat *> ba, bb, tca, tcb;
     for (int i = 0; i < count; ++i) {
         const int64_t m = A[i]->rows, l = A[i]->cols, n = B[i]->cols;
         const int base = o.base == GF2_BASE_AUTO ? GF2_BASE_M4RM : o.base;
@@ -755,10 +756,18 @@ int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[], const gf2_m
             bc.push_back(C[i]);
             ba.push_back(A[i]);
             bb.push_back(B[i]);
+        } else if (base == GF2_BASE_TC_FP8 && depth == 0 && tc_fp8_available()) {
+            tcc.push_back(C[i]);
+            tca.push_back(A[i]);
+            tcb.push_back(B[i]);
         } else {
             rc = gf2_mul(C[i], A[i], B[i], &o, stream);
             if (rc) return rc;
         }
+    }
+    if (!tcc.empty()) {
+        rc = gf2::tc_batched_mul(tcc.data(), tca.data(), tcb.data(), (int)tcc.size(), o.accumulate, s);
+        if (rc) return rc;
     }
     if (bc.empty()) return GF2_OK;
     int ch = -1;

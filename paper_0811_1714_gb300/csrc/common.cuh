@@ -145,6 +145,11 @@ const char *batched_variant_name(int i);
 void batched_release();
 int tc_status_read_and_clear(unsigned int *out, cudaStream_t s);
 int wait_selftest_launch(long long limit, cudaStream_t s);
+// Batched products of uneven shapes on the tensor-core base case (one
+// batched transpose + one persistent launch, graph-replayed).
+int tc_batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[], int count,
+                   int accumulate, cudaStream_t s);
+void tc_batched_release();
 bool tc_fp8_available();
 
 }  // namespace gf2
