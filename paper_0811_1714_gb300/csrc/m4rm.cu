@@ -52,20 +52,45 @@ struct Params {
     int mode;                   // 0: store, 1: C ^= (plain), 2: atomic XOR
 };
 
-template <int KB, int NT, int R, int NWARP>
+// Tensor-memory spill of half a tile (Blackwell TMEM, 512 columns x 128
+// lanes x 32 bits per SM): 8 row-groups of a thread = 32 columns of its lane.
+__device__ __forceinline__ void tm_st32(uint32_t taddr, const uint4 (&v)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+                 ::"r"(taddr), "r"(v[0].x), "r"(v[0].y), "r"(v[0].z), "r"(v[0].w), "r"(v[1].x), "r"(v[1].y), "r"(v[1].z), "r"(v[1].w), "r"(v[2].x), "r"(v[2].y), "r"(v[2].z), "r"(v[2].w), "r"(v[3].x), "r"(v[3].y), "r"(v[3].z), "r"(v[3].w), "r"(v[4].x), "r"(v[4].y), "r"(v[4].z), "r"(v[4].w), "r"(v[5].x), "r"(v[5].y), "r"(v[5].z), "r"(v[5].w), "r"(v[6].x), "r"(v[6].y), "r"(v[6].z), "r"(v[6].w), "r"(v[7].x), "r"(v[7].y), "r"(v[7].z), "r"(v[7].w) : "memory");
+}
+__device__ __forceinline__ void tm_ld32(uint32_t taddr, uint4 (&v)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                 : "=r"(v[0].x), "=r"(v[0].y), "=r"(v[0].z), "=r"(v[0].w), "=r"(v[1].x), "=r"(v[1].y), "=r"(v[1].z), "=r"(v[1].w), "=r"(v[2].x), "=r"(v[2].y), "=r"(v[2].z), "=r"(v[2].w), "=r"(v[3].x), "=r"(v[3].y), "=r"(v[3].z), "=r"(v[3].w), "=r"(v[4].x), "=r"(v[4].y), "=r"(v[4].z), "=r"(v[4].w), "=r"(v[5].x), "=r"(v[5].y), "=r"(v[5].z), "=r"(v[5].w), "=r"(v[6].x), "=r"(v[6].y), "=r"(v[6].z), "=r"(v[6].w), "=r"(v[7].x), "=r"(v[7].y), "=r"(v[7].z), "=r"(v[7].w) : "r"(taddr) : "memory");
+}
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// One CTA: a tile of BM rows x 1024 columns of C.  With TM (tall tiles),
+// the tile has two halves of NWARP*4*R rows: one in registers, the other in
+// tensor memory; the halves swap once per pass, after the first half's
+// lookups, so the tables of a pass serve twice the rows (table cost /
+// lookup cost = 2^k / BM halves) for one store + load of half a tile.
+template <int KB, int NT, int R, int NWARP, bool TM>
 __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
 {
     constexpr int NTH = NWARP * 32;
     constexpr int KG = KB * NT;          // rows of B per pass = bits of each A row per pass
     constexpr int TROWS = 1 << KB;
-    constexpr int BM = NWARP * 4 * R;
+    constexpr int HM = NWARP * 4 * R;    // rows held in registers
+    constexpr int BM = TM ? 2 * HM : HM;
     constexpr unsigned IMASK = (1u << KB) - 1u;
     static_assert(KG <= 64, "a pass reads at most 64 bits of a row of A");
+    static_assert(!TM || (NWARP == 8 && R == 32), "tensor-memory halves: 8 warps x 128 columns per slot");
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);        // NT * TROWS * 8
     uint4 *stg = tab + NT * TROWS * LPR;                       // 2 * KG * 8   (B rows of a pass)
     uint4 *sta = stg + 2 * KG * LPR;                           // 2 * BM       (A words of a pass)
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sta + 2 * BM);
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -92,9 +117,49 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
 
     const int trow = warp * 4 * R + (lane >> 3);               // tile row of row-group r: trow + 4r
 
+    // tensor memory: warp w owns lanes 32 (w % 4) .. +31 and the 256 columns
+    // starting at 256 (w / 4), as two slots of 128 columns (R row-groups)
+    uint32_t t_other = 0, t_free = 0;
+    if constexpr (TM) {
+        if (warp == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;"
+                         ::"r"((uint32_t)__cvta_generic_to_shared(tslot)) : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        const uint32_t tb = *tslot + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 256);
+        t_other = tb;
+        t_free = tb + 128;
+    }
+    bool have_other = false;     // the half in tensor memory has been written
+    int cur = 0;                 // the half in registers
+
     uint4 acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+
+    // registers <-> tensor memory: park the current half, fetch the other
+    auto swap_halves = [&]() {
+#pragma unroll
+        for (int j = 0; j < R / 8; ++j)
+            tm_st32(t_free + 32 * j, *reinterpret_cast<const uint4(*)[8]>(&acc[8 * j]));
+        tm_wait_st();
+        if (have_other) {
+#pragma unroll
+            for (int j = 0; j < R / 8; ++j) tm_ld32(t_other + 32 * j, *reinterpret_cast<uint4(*)[8]>(&acc[8 * j]));
+            tm_wait_ld();
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+        }
+        have_other = true;
+        const uint32_t t = t_other;
+        t_other = t_free;
+        t_free = t;
+        cur ^= 1;
+    };
 
     // Stage pass g: its KG rows of B (tile columns) and the words of each
     // tile row of A that hold columns g*KG .. g*KG+KG-1.  When KG divides 128
@@ -141,6 +206,62 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
         cp_async_commit();
     };
 
+    // ReadBits + AddRowFromTable for NT tables (Algorithms 1 and 3) on the
+    // rows of half h of the tile, pass g
+    auto lookups = [&](int g, int buf, int h) {
+        const int64_t kb = (int64_t)g * KG;
+        const int64_t wa = kb >> 6;
+        const int sh = (int)(kb & 63);
+        const uint64_t mlo = word_mask(wa, P.l);
+        const uint64_t mhi = (sh + KG > 64) ? word_mask(wa + 1, P.l) : 0ull;
+        const uint4 *arow = sta + (CHUNKED_A ? ((g / PPC) & 1) : buf) * BM + h * HM + trow;
+        const int aoff = CHUNKED_A ? (int)(wa & 1) : 0;          // word inside the staged chunk
+        if constexpr (CHUNKED_A && KG <= 32 && !TM) {
+            // the pass's KG bits of a row lie in one 32-bit half of the
+            // staged chunk: read them for every row-group first, so that
+            // the lookups below do not wait on these loads
+            const uint32_t *a32 = reinterpret_cast<const uint32_t *>(arow) + 2 * aoff + (sh >> 5);
+            const int s32 = sh & 31;
+            const uint32_t am = (uint32_t)(mlo >> (sh & 32)) >> s32;
+            uint32_t ab[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) ab[r] = (a32[16 * r] >> s32) & am;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                uint4 a = acc[r];
+#pragma unroll
+                for (int ti = 0; ti < NT; ++ti) {
+                    const unsigned x = (ab[r] >> (ti * KB)) & IMASK;
+                    a = x4(a, tab[(ti * TROWS + (int)x) * LPR + chunk]);
+                }
+                acc[r] = a;
+                // keeps the compiler from hoisting the loads of later
+                // row-groups: t loads in flight per warp already saturate
+                // shared memory
+                asm volatile("" ::: "memory");
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const uint2 aw = reinterpret_cast<const uint2 *>(&arow[4 * r])[aoff];
+                const uint64_t lo = ((uint64_t)aw.y << 32 | aw.x) & mlo;
+                uint64_t bits = lo >> sh;
+                if (!CHUNKED_A && sh + KG > 64) {
+                    const uint2 aw2 = reinterpret_cast<const uint2 *>(&arow[4 * r])[1];
+                    bits |= (((uint64_t)aw2.y << 32 | aw2.x) & mhi) << (64 - sh);
+                }
+                uint4 a = acc[r];
+#pragma unroll
+                for (int ti = 0; ti < NT; ++ti) {
+                    const unsigned x = (unsigned)(bits >> (ti * KB)) & IMASK;
+                    a = x4(a, tab[(ti * TROWS + (int)x) * LPR + chunk]);
+                }
+                acc[r] = a;
+                asm volatile("" ::: "memory");
+            }
+        }
+    };
+
     // the first pass stages the A chunk holding it (a K split may start
     // inside a chunk); every later chunk is staged one pass before its first
     if (g_begin < g_end) issue_stage(g_begin, 0, true);
@@ -156,39 +277,18 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
         }
         build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
         __syncthreads();                       // tables complete
-        // ReadBits + AddRowFromTable for NT tables (Algorithms 1 and 3).
-        const int64_t kb = (int64_t)g * KG;
-        const int64_t wa = kb >> 6;
-        const int sh = (int)(kb & 63);
-        const uint64_t mlo = word_mask(wa, P.l);
-        const uint64_t mhi = (sh + KG > 64) ? word_mask(wa + 1, P.l) : 0ull;
-        const uint4 *arow = sta + (CHUNKED_A ? ((g / PPC) & 1) : buf) * BM + trow;
-        const int aoff = CHUNKED_A ? (int)(wa & 1) : 0;          // word inside the staged chunk
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint2 aw = reinterpret_cast<const uint2 *>(&arow[4 * r])[aoff];
-            const uint64_t lo = ((uint64_t)aw.y << 32 | aw.x) & mlo;
-            uint64_t bits = lo >> sh;
-            if (!CHUNKED_A && sh + KG > 64) {
-                const uint2 aw2 = reinterpret_cast<const uint2 *>(&arow[4 * r])[1];
-                bits |= (((uint64_t)aw2.y << 32 | aw2.x) & mhi) << (64 - sh);
-            }
-            uint4 a = acc[r];
-#pragma unroll
-            for (int ti = 0; ti < NT; ++ti) {
-                const unsigned x = (unsigned)(bits >> (ti * KB)) & IMASK;
-                a = x4(a, tab[(ti * TROWS + (int)x) * LPR + chunk]);
-            }
-            acc[r] = a;
-            // keeps the compiler from hoisting the loads of later row-groups:
-            // t loads in flight per warp already saturate shared memory
-            asm volatile("" ::: "memory");
+        lookups(g, buf, cur);
+        if constexpr (TM) {
+            swap_halves();
+            lookups(g, buf, cur);
         }
     }
 
-    // write the C tile: one loop per mode so that the row loop stays simple
-    if (cw < nW) {
-        const int64_t first = row0 + trow;
+    // write the C rows of half h from acc: one loop per mode so that the row
+    // loop stays simple
+    auto write_half = [&](int h) {
+        if (cw >= nW) return;
+        const int64_t first = row0 + h * HM + trow;
         const int64_t left = P.m - first;               // rows of this thread: first + 4r, r < R
         const int nrows = left <= 0 ? 0 : (left < 4 * R ? (int)left : 4 * R);
         uint64_t *cr = C + first * P.ldc + cw;
@@ -222,6 +322,24 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
                 }
             }
         }
+    };
+    write_half(cur);
+    if constexpr (TM) {
+        // the other half: from tensor memory, or zero if no pass ran
+        if (have_other) {
+#pragma unroll
+            for (int j = 0; j < R / 8; ++j) tm_ld32(t_other + 32 * j, *reinterpret_cast<uint4(*)[8]>(&acc[8 * j]));
+            tm_wait_ld();
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+        }
+        write_half(cur ^ 1);
+        tm_fence_before();
+        __syncthreads();
+        tm_fence_after();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(*tslot) : "memory");
     }
 }
 
@@ -274,17 +392,19 @@ struct Variant {
     int smem;
 };
 
-// Tile rows BM = 4 * R * NW.  Tall tiles (BM = 1024) use 8 warps holding
-// 32 row-groups each (128 accumulator registers per thread, no spills).
-template <int KB, int NT, int R, int NW>
+// Tile rows BM = 4 * R * NW (twice that with the tensor-memory half).
+// Tall tiles use 8 warps holding 32 row-groups each (128 accumulator
+// registers per thread, no spills).
+template <int KB, int NT, int R, int NW, bool TM = false>
 Variant make_variant()
 {
-    constexpr int BM = 4 * R * NW;
-    return Variant{KB, NT, BM, NW, &m4rm_kernel<KB, NT, R, NW>,
-                   (int)(NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16)};
+    constexpr int BM = 4 * R * NW * (TM ? 2 : 1);
+    return Variant{KB, NT, BM, NW, &m4rm_kernel<KB, NT, R, NW, TM>,
+                   (int)(NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16 + (TM ? 16 : 0))};
 }
 
 const Variant kVariants[] = {
+    make_variant<8, 4, 32, 8, true>(),
     make_variant<8, 4, 32, 8>(), make_variant<8, 2, 32, 8>(), make_variant<7, 8, 32, 8>(),
     make_variant<6, 8, 32, 8>(), make_variant<9, 2, 32, 8>(), make_variant<10, 1, 32, 8>(),
     make_variant<5, 8, 32, 8>(), make_variant<4, 8, 32, 8>(),
@@ -321,23 +441,24 @@ static int sm_count()
     return n;
 }
 
-// Row-tile height and (k, t) for a shape: tall tiles (1024 rows) amortise
-// the 2^k-row table over many lookups (table cost / lookup cost = 2^k / BM,
-// Section 3.2's trade-off); small problems take shorter tiles and smaller k
-// so that every SM has work, and split K when even that is not enough.
+// Row-tile height and (k, t) for a shape: tall tiles (2048 rows, half of
+// them in tensor memory, then 1024) amortise the 2^k-row table over many
+// lookups (table cost / lookup cost = 2^k / BM, Section 3.2's trade-off);
+// small problems take shorter tiles and smaller k so that every SM has
+// work, and split K when even that is not enough.
 void m4rm_pick(int64_t m, int64_t l, int64_t n, int batch, int *k, int *t, int *bm, int *ksplit)
 {
     const int sms = sm_count();
     const int64_t tn = (words_of(n) + TILE_WORDS - 1) / TILE_WORDS;
-    const int bms[3] = {1024, 256, 64};
+    const int bms[4] = {2048, 1024, 256, 64};
     int b = 1024;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         b = bms[i];
         const int64_t ctas = (int64_t)batch * tn * ((m + b - 1) / b);
         if (ctas >= 2 * sms) break;
     }
-    int kk = (b == 1024) ? 8 : (b == 256 ? 6 : 4);
-    int tt = (b == 1024) ? 4 : 8;
+    int kk = (b >= 1024) ? 8 : (b == 256 ? 6 : 4);
+    int tt = (b >= 1024) ? 4 : 8;
     if (*k > 0 || *t > 0) {
         if (*k > 0) kk = *k;
         tt = *t;

@@ -95,6 +95,31 @@ def test_m4rm_density_09_and_accumulate():
     assert_same_bits(to_host(Cd), ref ^ C0, n, "accumulate")
 
 
+@pytest.mark.parametrize("accumulate", [0, 1])
+def test_m4rm_tall_tiles_with_tensor_memory_half(accumulate):
+    """2048-row tiles (one half in registers, one in tensor memory): rows
+    ragged at the tile end and checked across the half boundary (row 1024),
+    columns ragged in the last tile, K not a multiple of the 32-bit pass."""
+    m, l, n = 2 * 2048 + 77, 333, 159 * 1024 + 200
+    plan = g.gf2_describe_plan(m, l, n, g.opts(base=g.GF2_BASE_M4RM, depth=0))
+    assert "tile_rows=2048" in plan, plan
+    A, B = inputs(m, l, n, seeds=(41, 42))
+    C0 = synth.random_packed(m, n, 43) if accumulate else None
+    Ad, Bd = to_dev(A), to_dev(B)
+    Cd = to_dev(C0) if accumulate else g.empty(m, n)
+    if not accumulate:
+        Cd.fill_(-1)
+    g.gf2_mul(g.mat(Cd, n), g.mat(Ad, l), g.mat(Bd, n),
+              g.opts(base=g.GF2_BASE_M4RM, depth=0, accumulate=accumulate))
+    g.gf2_device_status()
+    got = to_host(Cd)
+    for r0, r1 in ((0, 40), (1000, 1050), (2030, 2080), (3060, 3090), (4096, m)):
+        ref = oracle.mul_packed(np.ascontiguousarray(A[r0:r1]), B, r1 - r0, l, n)
+        if accumulate:
+            ref = ref ^ C0[r0:r1]
+        assert_same_bits(got[r0:r1], ref, n, "rows %d..%d" % (r0, r1))
+
+
 def test_tail_garbage_is_ignored():
     m, l, n = 300, 200, 333
     A, B = inputs(m, l, n)
