@@ -454,6 +454,7 @@ void m4rm_pick(int64_t m, int64_t l, int64_t n, int batch, int *k, int *t, int *
     int b = 1024;
     for (int i = 0; i < 4; ++i) {
         b = bms[i];
+        if (b == 2048 && m <= 1024) continue;       // the tensor-memory half would hold no rows
         const int64_t ctas = (int64_t)batch * tn * ((m + b - 1) / b);
         if (ctas >= 2 * sms) break;
     }
