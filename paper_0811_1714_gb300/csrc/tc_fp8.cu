@@ -3,36 +3,49 @@
 //
 // Why it is exact (Section 2.3): a GF(2) dot product is an AND followed by an
 // XOR accumulation, i.e. the parity of the INTEGER dot product of the 0/1
-// vectors.  Each bit is unpacked to the FP8 E4M3 value 2^-6 (byte 0x08) or 0,
-// so every product is 2^-12 or 0 and a dot product over a K-chunk of at most
-// KCHUNK = 4096 entries is count * 2^-12 with count <= 2^12: a multiple of
-// 2^-12 below 2 that any accumulator keeping 13 or more significant bits
-// holds exactly.  After each chunk the FP32 accumulator D is read from tensor
-// memory and the parity of count is the last mantissa bit of D + 2048 (whose
-// ulp is 2^-12); parities of successive chunks are XORed, which is the
-// GF(2) sum over the whole K range.
+// vectors.  Each bit becomes one FP8 E4M3 byte, 0 for a 0-bit and a power of
+// two for a 1-bit that depends on the entry's K index mod 4 (i): 2^(i-9) in
+// A (bytes 0x01, 0x02, 0x04, 0x08) and 2^(-6-i) in B (0x08, 0x04, 0x02,
+// 0x01).  Every product of two 1-bits is therefore exactly 2^-15, and a dot
+// product over a K-chunk of at most KCHUNK = 4096 entries is count * 2^-15
+// <= 2^-3 with count <= 2^12: a multiple of 2^-15 that any accumulator
+// keeping 13 or more significant bits holds exactly.  After each chunk the
+// FP32 accumulator D is read from tensor memory and the parity of count is
+// the last mantissa bit of D + 256 (whose ulp is 2^-15); parities of
+// successive chunks are XORed, which is the GF(2) sum over the whole K range.
+// The position-dependent values let a byte of bits expand with one byte
+// permute and one mask per 4 entries (B's bits are first reversed, so the
+// mask picks them in the opposite order).
 //
-// Layout of one CTA (persistent, one per SM, 18 warps):
-//   warps 0-3   epilogue: tcgen05.ld of the 128 x 256 FP32 accumulator (warp
+// Layout of one CTA (persistent, one per SM, 22 warps):
+//   warps 0-3   epilogue: tcgen05.ld of the 128 x 192 FP32 accumulator (warp
 //               w reads TMEM lanes 32w..32w+31 = rows of the tile), parity,
 //               packed 64-bit words of C;
-//   warp 4      TMEM allocation (512 columns = two accumulators) and the MMA
-//               issuer (one thread): tcgen05.mma.cta_group::1.kind::f8f6f4,
-//               M = 128, N = 256, K = 32 per instruction;
+//   warp 4      TMEM allocation (all 512 columns) and the MMA issuer (one
+//               thread): tcgen05.mma.cta_group::1.kind::f8f6f4 with A read
+//               from TENSOR MEMORY and B from shared memory, M = 128,
+//               N = 192, K = 32 per instruction;
 //   warp 5      TMA issuer (one thread): cp.async.bulk.tensor loads of the
-//               PACKED words of A (128 rows x 16 bytes) and B^T (256 rows x
+//               PACKED words of A (128 rows x 16 bytes) and B^T (192 rows x
 //               16 bytes) of a 128-entry K block into a ring of packed stages
 //               (rows beyond the matrices and words beyond K arrive as zeros);
-//   warps 6-17  unpackers: read a packed stage, expand every bit to one FP8
-//               byte (a byte of bits -> 8 FP8 bytes through a bank-conflict-
-//               free table in shared memory) and store the tile in the
-//               128-byte-swizzled K-major layout the MMA reads.
+//   warps 6-9   A unpackers, one per TMEM lane quarter: each thread expands
+//               the 128 bits of its row of A into 128 FP8 bytes in registers
+//               and stores them with tcgen05.st (lane = row, 4 K entries per
+//               32-bit column), so A never occupies shared memory;
+//   warps 10-21 B unpackers: expand B^T's bits into FP8 bytes and store the
+//               tile in the 128-byte-swizzled K-major layout the MMA reads.
+// Tensor memory: accumulators at columns 0 and 256 (192 columns each), four
+// A stages of 32 columns at 192, 224, 448, 480.
+// Bits are expanded in registers (4 bits -> 4 bytes by one byte permute and
+// one mask), so shared-memory bandwidth goes to the B stores and the tensor
+// core's B reads only.
 // Hand-offs use mbarriers: packed full (TMA transaction bytes) / packed empty,
-// unpacked full / empty (the MMA side signalled by tcgen05.commit), and
-// accumulator full / empty (MMA <-> epilogue).  Every wait is bounded; an
-// expired wait records GF2_ETIMEOUT in a device status word and the CTA winds
-// down (waits for its issued copies and MMAs, frees its tensor memory)
-// instead of hanging.
+// A full / empty and B full / empty (the MMA side signalled by
+// tcgen05.commit), and accumulator full / empty (MMA <-> epilogue).  Every
+// wait is bounded; an expired wait records GF2_ETIMEOUT in a device status
+// word and the CTA winds down (waits for its issued copies and MMAs, frees
+// its tensor memory) instead of hanging.
 #include "common.cuh"
 
 #include <cuda.h>
@@ -47,39 +60,41 @@ namespace gf2 {
 namespace {
 
 constexpr int BM = 128;            // rows of A per tile (MMA M)
-constexpr int BN = 256;            // rows of B^T per tile (MMA N)
-constexpr int BK = 128;            // K entries per stage (128 FP8 bytes = one swizzle row)
-constexpr int USTAGES = 3;         // unpacked (FP8) stages
+constexpr int BN = 192;            // rows of B^T per tile (MMA N; 3 words of C)
+constexpr int BK = 256;            // K entries per stage (two 128-byte swizzle rows of FP8)
+constexpr int KW = BK / 64;        // packed words per row per stage
+constexpr int STAGES = 2;          // unpacked stages (A in tensor memory, B in shared memory)
 constexpr int PSTAGES = 8;         // packed stages
 constexpr int KCHUNK = 4096;       // exact-sum bound (entries per accumulation)
 constexpr int KB_PER_CHUNK = KCHUNK / BK;
-constexpr int A_BYTES = BM * BK;   // 16 KB
-constexpr int B_BYTES = BN * BK;   // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int PA_BYTES = BM * 16;  // packed A block: 128 rows x 2 words
-constexpr int PB_BYTES = BN * 16;  // packed B^T block: 256 rows x 2 words
+constexpr int SUB_BYTES = BN * 128;          // B^T x 128 K entries (one swizzle-row sub-tile)
+constexpr int STAGE_BYTES = 2 * SUB_BYTES;   // 48 KB
+constexpr int PA_BYTES = BM * KW * 8;        // packed A block: 128 rows x 4 words
+constexpr int PB_BYTES = BN * KW * 8;        // packed B^T block: 192 rows x 4 words
 constexpr int PSTAGE_BYTES = PA_BYTES + PB_BYTES;
 constexpr int NUM_EPI_WARPS = 4;
 constexpr int MMA_WARP = 4;
 constexpr int TMA_WARP = 5;
+constexpr int AUNP_WARP0 = 6;      // four A unpackers, one per TMEM lane quarter
+constexpr int NUM_AUNP_WARPS = 4;
+constexpr int UNP_WARP0 = AUNP_WARP0 + NUM_AUNP_WARPS;         // B unpackers
 constexpr int NUM_UNP_WARPS = 12;
-constexpr int UNP_WARP0 = 6;
-constexpr int NTHREADS = (UNP_WARP0 + NUM_UNP_WARPS) * 32;     // 576
-constexpr int NUNP = NUM_UNP_WARPS * 32;                        // 384
-constexpr int UNP_ROWS = (2 * (BM + BN) + NUNP - 1) / NUNP;     // half rows per unpacker thread
+constexpr int NTHREADS = (UNP_WARP0 + NUM_UNP_WARPS) * 32;     // 704
+constexpr int NUNP = NUM_UNP_WARPS * 32;                        // 384 = 2 * BN half rows
+constexpr int UNP_ARRIVALS = NUM_AUNP_WARPS + NUM_UNP_WARPS;    // arrivals that fill a stage
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;        // clock64 cycles (~2 s)
+static_assert(NUNP == 2 * BN, "one half row of each 128-entry sub-tile per B unpacker thread");
+static_assert(AUNP_WARP0 % 4 == 2 && NUM_AUNP_WARPS == 4, "A unpackers cover the four lane quarters");
 
-// Byte -> 8 FP8 bytes through a table in shared memory: 256 entries of 8
-// bytes, replicated 16 times and interleaved (entry e of copy j at 8-byte
-// slot 16e + j) so that lane j of a half-warp always reads bank pair j:
-// conflict free whatever the bytes are.
-constexpr int LUT_COPIES = 16;
-constexpr int LUT_BYTES = 256 * LUT_COPIES * 8;   // 32 KB
+// tensor memory: accumulators at columns 0 and 256 (192 columns each), A
+// stages of 64 columns (256 K entries) at 192 and 448
+__host__ __device__ constexpr uint32_t acc_col(int b) { return (uint32_t)b * 256u; }
+__host__ __device__ constexpr uint32_t a_col(int s) { return (uint32_t)s * 256u + 192u; }
 
-// barriers: pfull[P], pempty[P], ufull[U], uempty[U], tfull[2], tempty[2], done
-constexpr int NBARS = 2 * PSTAGES + 2 * USTAGES + 5;
-constexpr int SMEM_BYTES = USTAGES * STAGE_BYTES + PSTAGES * PSTAGE_BYTES + LUT_BYTES + NBARS * 8 + 16 + 1024;
+// barriers: pfull[P], pempty[P], full[S], empty[S], tfull[2], tempty[2], done
+constexpr int NBARS = 2 * PSTAGES + 2 * STAGES + 5;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + PSTAGES * PSTAGE_BYTES + NBARS * 8 + 16 + 1024;
 static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
 
 // One product of a batch of uneven shapes: tensor maps of its packed A and
@@ -220,13 +235,15 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
+// D (+)= A B^T with A in tensor memory (lane = row of A, 4 FP8 entries of K
+// per 32-bit column, 8 columns per K = 32) and B^T in shared memory.
+__device__ __forceinline__ void mma_f8_ta(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t acc)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc)
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}"
+        ::"r"(dtmem), "r"(atmem), "l"(bdesc), "r"(IDESC), "r"(acc)
         : "memory");
 }
 
@@ -256,8 +273,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// 4 bits -> 4 FP8 bytes (0x08 for a 1-bit): bit b lands on bit 8b + 3.
-__device__ __forceinline__ uint32_t spread4(uint32_t x4) { return (x4 * 0x01020408u) & 0x08080808u; }
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+                 ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31]) : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// A: 32 bits x (K entries 32h .. 32h+31) -> 8 words of 4 FP8 bytes; byte i
+// of word n is entry 4n+i: bit 4n+i of x moved to bit i (value 2^(i-9)).
+// The byte holding the nibble is replicated by a byte permute and the mask
+// keeps bit i of copy i.
+__device__ __forceinline__ void expand_a(uint32_t x, uint32_t *out)
+{
+    const uint32_t xs = x >> 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        out[2 * k] = __byte_perm(x, 0, 0x1111u * k) & 0x08040201u;
+        out[2 * k + 1] = __byte_perm(xs, 0, 0x1111u * k) & 0x08040201u;
+    }
+}
+
+// B: as expand_a with bit 4n+i moved to bit 3-i (value 2^(-6-i)).  In the
+// bit-reversed word r, nibble n of x is nibble 7-n with its bits reversed,
+// so replicating its byte and masking bit 3-i of copy i does it.
+__device__ __forceinline__ uint32_t expand_b_nibble(uint32_t r, uint32_t rs, int n)
+{
+    const int m = 7 - n;                       // nibble of r
+    return __byte_perm((m & 1) ? rs : r, 0, 0x1111u * (uint32_t)(m >> 1)) & 0x01020408u;
+}
 
 // Tile t -> (batch, tile row, tile column).
 __device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, int &tm, int &tn)
@@ -300,9 +345,8 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *sbase = smem_raw + (base - raw);
-    unsigned char *pbase = sbase + USTAGES * STAGE_BYTES;                    // packed ring
-    uint2 *lut = reinterpret_cast<uint2 *>(pbase + PSTAGES * PSTAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(lut) + LUT_BYTES);
+    unsigned char *pbase = sbase + STAGES * STAGE_BYTES;                     // packed ring
+    uint64_t *bars = reinterpret_cast<uint64_t *>(pbase + PSTAGES * PSTAGE_BYTES);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -311,20 +355,20 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     const uint32_t bar0 = smem_u32(bars);
     auto pfull_bar = [&](int s) { return bar0 + 8u * s; };
     auto pempty_bar = [&](int s) { return bar0 + 8u * (PSTAGES + s); };
-    auto ufull_bar = [&](int s) { return bar0 + 8u * (2 * PSTAGES + s); };
-    auto uempty_bar = [&](int s) { return bar0 + 8u * (2 * PSTAGES + USTAGES + s); };
-    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * USTAGES + b); };
-    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * USTAGES + 2 + b); };
-    const uint32_t done_bar = bar0 + 8u * (2 * PSTAGES + 2 * USTAGES + 4);
+    auto full_bar = [&](int s) { return bar0 + 8u * (2 * PSTAGES + s); };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (2 * PSTAGES + STAGES + s); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * STAGES + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * PSTAGES + 2 * STAGES + 2 + b); };
+    const uint32_t done_bar = bar0 + 8u * (2 * PSTAGES + 2 * STAGES + 4);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < PSTAGES; ++s) {
             mbar_init(pfull_bar(s), 1);                   // the TMA thread's expect_tx arrival
-            mbar_init(pempty_bar(s), NUM_UNP_WARPS);
+            mbar_init(pempty_bar(s), UNP_ARRIVALS);
         }
-        for (int s = 0; s < USTAGES; ++s) {
-            mbar_init(ufull_bar(s), NUM_UNP_WARPS);       // one arrival per unpacker warp
-            mbar_init(uempty_bar(s), 1);                  // tcgen05.commit
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), UNP_ARRIVALS);         // one arrival per unpacker warp (A and B)
+            mbar_init(empty_bar(s), 1);                   // tcgen05.commit
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull_bar(b), 1);
@@ -334,10 +378,6 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    for (int i = threadIdx.x; i < 256 * LUT_COPIES; i += NTHREADS) {
-        const uint32_t e = (uint32_t)(i / LUT_COPIES);
-        lut[i] = make_uint2(spread4(e & 0xF), spread4(e >> 4));
     }
     if (warp == MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -350,7 +390,7 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     const uint32_t tmem_base = *tmem_slot;
 
     // every role walks the CTA's tiles t = blockIdx.x, +gridDim.x, ... and,
-    // inside a tile, its K blocks; q counts stage uses in that order
+    // inside a tile, its K blocks; q counts K blocks in that order
 
     if (warp == TMA_WARP) {
         // ------------------------------------------------------------ TMA issuer
@@ -374,8 +414,8 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     if (!mbar_wait(pempty_bar(ps), (uint32_t)((q / PSTAGES) & 1) ^ 1u, P.status, abort_flag)) { ok = false; break; }
                     const uint32_t dst = smem_u32(pbase + ps * PSTAGE_BYTES);
                     mbar_arrive_expect_tx(pfull_bar(ps), PSTAGE_BYTES);
-                    tma_load_3d(dst, T.ma, (int)(kb * 2), T.tm * BM, T.z, pfull_bar(ps));
-                    tma_load_3d(dst + PA_BYTES, T.mb, (int)(kb * 2), T.tn * BN, T.z, pfull_bar(ps));
+                    tma_load_3d(dst, T.ma, (int)(kb * KW), T.tm * BM, T.z, pfull_bar(ps));
+                    tma_load_3d(dst + PA_BYTES, T.mb, (int)(kb * KW), T.tn * BN, T.z, pfull_bar(ps));
                 }
             }
             // wind down: copies issued but not consumed (only after an abort)
@@ -384,50 +424,88 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 mbar_drain(pfull_bar((int)(r % PSTAGES)), (uint32_t)((r / PSTAGES) & 1), P.status);
         }
         __syncwarp();
-    } else if (warp >= UNP_WARP0) {
-        // ------------------------------------------------------------ unpackers
-        const int pt = threadIdx.x - UNP_WARP0 * 32;      // 0..NUNP-1
-        const uint2 *lutl = lut + (lane & (LUT_COPIES - 1));
+    } else if (warp >= AUNP_WARP0 && warp < UNP_WARP0) {
+        // ------------------------------------------------------------ A unpackers
+        // thread = row of the A tile = its TMEM lane (warp w owns lanes 32 (w % 4) ..)
+        const int row = (warp & 3) * 32 + lane;
+        const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
         int64_t q = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
           const TileInfo T = get_tile(P, &mapA, &mapB, t);
           for (int64_t kb = 0; kb < T.nkb; ++kb, ++q) {
             const int ps = (int)(q % PSTAGES);
-            const int us = (int)(q % USTAGES);
+            const int s = (int)(q % STAGES);
             if (!warp_wait(pfull_bar(ps), (uint32_t)((q / PSTAGES) & 1), P.status, abort_flag)) { ok = false; break; }
-            if (!warp_wait(uempty_bar(us), (uint32_t)((q / USTAGES) & 1) ^ 1u, P.status, abort_flag)) { ok = false; break; }
-            const unsigned char *pk = pbase + ps * PSTAGE_BYTES;   // A rows then B^T rows, 16 bytes each
-            unsigned char *st = sbase + us * STAGE_BYTES;
+            if (!warp_wait(empty_bar(s), (uint32_t)((q / STAGES) & 1) ^ 1u, P.status, abort_flag)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t *pk = reinterpret_cast<const uint64_t *>(pbase + ps * PSTAGE_BYTES) + KW * row;
+            const uint32_t ta = tmem_base + tlane + a_col(s);
 #pragma unroll
-            for (int j = 0; j < UNP_ROWS; ++j) {
-                const int hr = pt + j * NUNP;              // half rows: 256 of A, then 512 of B^T
-                if (hr >= 2 * (BM + BN)) continue;
-                const int row = hr >> 1, half = hr & 1;
+            for (int h = 0; h < 2; ++h) {
                 // words beyond K arrive as zeros; bits beyond K in the last word are masked
-                const uint64_t wv = reinterpret_cast<const uint64_t *>(pk)[hr] & word_mask(kb * 2 + half, T.l);
-                unsigned char *rowp = (row < BM) ? (st + (row >> 3) * 1024 + (row & 7) * 128)
-                                                 : (st + A_BYTES + ((row - BM) >> 3) * 1024 + ((row - BM) & 7) * 128);
-                const int sw = row & 7;                    // (row - BM) & 7 == row & 7
-                const uint32_t lo = (uint32_t)wv, hi = (uint32_t)(wv >> 32);
+                const uint64_t w0 = pk[2 * h] & word_mask(kb * KW + 2 * h, T.l);
+                const uint64_t w1 = pk[2 * h + 1] & word_mask(kb * KW + 2 * h + 1, T.l);
+                uint32_t v[32];                        // K entries 128h + 4j .. 4j+3 in v[j]
+                expand_a((uint32_t)w0, v);
+                expand_a((uint32_t)(w0 >> 32), v + 8);
+                expand_a((uint32_t)w1, v + 16);
+                expand_a((uint32_t)(w1 >> 32), v + 24);
+                tmem_st32(ta + 32 * h, v);
+                tmem_wait_st();
+            }
+            // the stores are complete: order them before the arrival the MMA
+            // thread acquires, then hand the packed stage back
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(full_bar(s));
+                mbar_arrive(pempty_bar(ps));
+            }
+          }
+        }
+    } else if (warp >= UNP_WARP0) {
+        // ------------------------------------------------------------ B unpackers
+        // thread pt: half row pt of each 128-entry sub-tile (row pt / 2)
+        const int pt = threadIdx.x - UNP_WARP0 * 32;      // 0..NUNP-1
+        const int row = pt >> 1, half = pt & 1;
+        const int sw = row & 7;
+        const int rowoff = (row >> 3) * 1024 + (row & 7) * 128;
+        int64_t q = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+          const TileInfo T = get_tile(P, &mapA, &mapB, t);
+          for (int64_t kb = 0; kb < T.nkb; ++kb, ++q) {
+            const int ps = (int)(q % PSTAGES);
+            const int s = (int)(q % STAGES);
+            if (!warp_wait(pfull_bar(ps), (uint32_t)((q / PSTAGES) & 1), P.status, abort_flag)) { ok = false; break; }
+            if (!warp_wait(empty_bar(s), (uint32_t)((q / STAGES) & 1) ^ 1u, P.status, abort_flag)) { ok = false; break; }
+            const uint64_t *pk = reinterpret_cast<const uint64_t *>(pbase + ps * PSTAGE_BYTES + PA_BYTES) + KW * row;
+            unsigned char *st = sbase + s * STAGE_BYTES + rowoff;
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {            // 16 entries -> one 16-byte chunk
-                    const uint32_t bits = qq < 2 ? lo : hi;
-                    const uint32_t b0 = __byte_perm(bits, 0, 0x4440 | ((qq & 1) * 2));
-                    const uint32_t b1 = __byte_perm(bits, 0, 0x4441 | ((qq & 1) * 2));
-                    const uint2 e0 = lutl[b0 * LUT_COPIES];
-                    const uint2 e1 = lutl[b1 * LUT_COPIES];
-                    const int chunk = (half * 4 + qq) ^ sw; // 128-byte swizzle
-                    *reinterpret_cast<uint4 *>(rowp + chunk * 16) = make_uint4(e0.x, e0.y, e1.x, e1.y);
+            for (int sub = 0; sub < 2; ++sub) {
+                const uint64_t wv = pk[2 * sub + half] & word_mask(kb * KW + 2 * sub + half, T.l);
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const uint32_t r = __brev((uint32_t)(wv >> (32 * hh)));
+                    const uint32_t rs = r >> 4;
+#pragma unroll
+                    for (int q2 = 0; q2 < 2; ++q2) {        // 16 entries -> one 16-byte chunk
+                        const int qq = 2 * hh + q2;
+                        const int chunk = (half * 4 + qq) ^ sw;   // 128-byte swizzle
+                        *reinterpret_cast<uint4 *>(st + sub * SUB_BYTES + chunk * 16) =
+                            make_uint4(expand_b_nibble(r, rs, 4 * q2), expand_b_nibble(r, rs, 4 * q2 + 1),
+                                       expand_b_nibble(r, rs, 4 * q2 + 2), expand_b_nibble(r, rs, 4 * q2 + 3));
+                    }
                 }
             }
             // each lane makes its stores visible to the tensor core (async
-            // proxy), then one arrival per warp on the unpacked stage, and
-            // the packed stage is handed back to the TMA thread
+            // proxy), then one arrival per warp on the stage, and the packed
+            // stage is handed back to the TMA thread
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(ufull_bar(us));
+                mbar_arrive(full_bar(s));
                 mbar_arrive(pempty_bar(ps));
             }
           }
@@ -435,7 +513,7 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t it = 0, u = 0;                        // stage uses, accumulator units
+            uint32_t it = 0, u = 0;                        // K blocks, accumulator units
             bool ok = true;
             for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
                 const TileInfo T = get_tile(P, &mapA, &mapB, t);
@@ -445,22 +523,23 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     const int ab = (int)(u & 1u);
                     if (!mbar_wait(tempty_bar(ab), ((u >> 1) & 1u) ^ 1u, P.status, abort_flag)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t dt = tmem_base + (uint32_t)(ab * BN);
-                    const int64_t kb0 = (int64_t)c * KB_PER_CHUNK;
-                    const int64_t kb1 = min(nkb, kb0 + KB_PER_CHUNK);
-                    for (int64_t kb = kb0; kb < kb1; ++kb, ++it) {
-                        const int s = (int)(it % USTAGES);
-                        if (!mbar_wait(ufull_bar(s), (it / USTAGES) & 1u, P.status, abort_flag)) { ok = false; break; }
+                    const uint32_t dt = tmem_base + acc_col(ab);
+                    const int kb0 = c * KB_PER_CHUNK;
+                    const int kb1 = (int)min(nkb, (int64_t)kb0 + KB_PER_CHUNK);
+                    for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = (int)(it & (STAGES - 1));
+                        if (!mbar_wait(full_bar(s), (it / STAGES) & 1u, P.status, abort_flag)) { ok = false; break; }
                         tc_fence_after();
-                        const uint32_t sa = base + s * STAGE_BYTES;
-                        const uint32_t sb = sa + A_BYTES;
+                        const uint32_t sb = base + s * STAGE_BYTES;
+                        const uint32_t ta = tmem_base + a_col(s);
 #pragma unroll
                         for (int kk = 0; kk < BK / 32; ++kk) {
-                            // K step of 32 FP8 entries = 32 bytes inside the swizzle row
-                            mma_f8(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
-                                   (kb > kb0 || kk > 0) ? 1u : 0u);
+                            // K step of 32 FP8 entries: 8 TMEM columns of A,
+                            // 32 bytes inside a swizzle row of B's sub-tile
+                            mma_f8_ta(dt, ta + 8 * kk, smem_desc_sw128(sb + (kk >> 2) * SUB_BYTES + (kk & 3) * 32),
+                                      (kb > kb0 || kk > 0) ? 1u : 0u);
                         }
-                        mma_commit(uempty_bar(s));         // stage free once these MMAs have read it
+                        mma_commit(empty_bar(s));          // stage free once these MMAs have read it
                     }
                     if (!ok) break;
                     mma_commit(tfull_bar(ab));             // accumulator ready for the epilogue
@@ -486,7 +565,7 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 const int ab = (int)(u & 1u);
                 if (!warp_wait(tfull_bar(ab), (u >> 1) & 1u, P.status, abort_flag)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * BN);
+                const uint32_t taddr = tmem_base + ((uint32_t)(warp * 32) << 16) + acc_col(ab);
 #pragma unroll 1
                 for (int g = 0; g < BN / 32; ++g) {
                     uint32_t r[32];
@@ -495,8 +574,8 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     uint32_t word = 0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        // D = count * 2^-12 < 2: the ulp of D + 2048 is 2^-12
-                        const uint32_t f = __float_as_uint(__uint_as_float(r[j]) + 2048.0f);
+                        // D = count * 2^-15 <= 2^-3: the ulp of D + 256 is 2^-15
+                        const uint32_t f = __float_as_uint(__uint_as_float(r[j]) + 256.0f);
                         word |= (f & 1u) << j;
                     }
                     par[g] ^= word;
@@ -578,7 +657,7 @@ EncodeFn encode_fn()
 
 // 3-D map over packed words: x = word in the row (extent ceil(l/64): words
 // beyond K are filled with zeros), y = row (extent rows), z = product of the
-// batch.  Box: 2 words x box_rows x 1.
+// batch.  Box: KW words x box_rows x 1.
 int make_map(CUtensorMap *map, const uint64_t *base, int64_t words, int64_t rows, int64_t ld, int batch,
              int64_t bs, int box_rows)
 {
@@ -587,7 +666,7 @@ int make_map(CUtensorMap *map, const uint64_t *base, int64_t words, int64_t rows
     const cuuint64_t dims[3] = {(cuuint64_t)words, (cuuint64_t)rows, (cuuint64_t)batch};
     const int64_t bstride = batch > 1 ? bs * 8 : rows * ld * 8;
     const cuuint64_t strides[2] = {(cuuint64_t)(ld * 8), (cuuint64_t)(bstride > 0 ? bstride : ld * 8)};
-    const cuuint32_t box[3] = {2u, (cuuint32_t)box_rows, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)KW, (cuuint32_t)box_rows, 1u};
     const cuuint32_t estr[3] = {1u, 1u, 1u};
     const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<uint64_t *>(base), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
