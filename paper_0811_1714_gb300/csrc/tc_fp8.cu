@@ -17,7 +17,7 @@
 // permute and one mask per 4 entries (B's bits are first reversed, so the
 // mask picks them in the opposite order).
 //
-// Layout of one CTA (persistent, one per SM, 22 warps):
+// Layout of one CTA (persistent, one per SM, 26 warps):
 //   warps 0-3   epilogue: tcgen05.ld of the 128 x 192 FP32 accumulator (warp
 //               w reads TMEM lanes 32w..32w+31 = rows of the tile), parity,
 //               packed 64-bit words of C;
@@ -26,23 +26,28 @@
 //               from TENSOR MEMORY and B from shared memory, M = 128,
 //               N = 192, K = 32 per instruction;
 //   warp 5      TMA issuer (one thread): cp.async.bulk.tensor loads of the
-//               PACKED words of A (128 rows x 16 bytes) and B^T (192 rows x
-//               16 bytes) of a 128-entry K block into a ring of packed stages
+//               PACKED words of A (128 rows x 32 bytes) and B^T (192 rows x
+//               32 bytes) of a 256-entry K block into a ring of packed stages
 //               (rows beyond the matrices and words beyond K arrive as zeros);
-//   warps 6-9   A unpackers, one per TMEM lane quarter: each thread expands
-//               the 128 bits of its row of A into 128 FP8 bytes in registers
-//               and stores them with tcgen05.st (lane = row, 4 K entries per
-//               32-bit column), so A never occupies shared memory;
-//   warps 10-21 B unpackers: expand B^T's bits into FP8 bytes and store the
-//               tile in the 128-byte-swizzled K-major layout the MMA reads.
-// Tensor memory: accumulators at columns 0 and 256 (192 columns each), four
-// A stages of 32 columns at 192, 224, 448, 480.
+//   warps 6-13  A unpackers, two per TMEM lane quarter: each thread expands
+//               128 bits of its row of A (half of a 256-entry K block) into
+//               128 FP8 bytes in registers and stores them with tcgen05.st
+//               (lane = row, 4 K entries per 32-bit column), so A never
+//               occupies shared memory;
+//   warps 14-25 B unpackers: expand B^T's bits into FP8 bytes and store the
+//               tile in the 128-byte-swizzled K-major layout the MMA reads
+//               (two 128-entry sub-tiles per K block).
+// Tensor memory: accumulators at columns 0 and 256 (192 columns each), two
+// A stages of 64 columns (256 K entries) at 192 and 448.
 // Bits are expanded in registers (4 bits -> 4 bytes by one byte permute and
 // one mask), so shared-memory bandwidth goes to the B stores and the tensor
 // core's B reads only.
 // Hand-offs use mbarriers: packed full (TMA transaction bytes) / packed empty,
-// A full / empty and B full / empty (the MMA side signalled by
-// tcgen05.commit), and accumulator full / empty (MMA <-> epilogue).  Every
+// stage full (every A and B unpacker warp arrives) / stage empty (one
+// tcgen05.commit per K block), and accumulator full / empty (MMA <->
+// epilogue).  A 256-entry K block gives the MMA thread eight MMAs per wait
+// and per commit: the issue of tcgen05.mma is close to synchronous, so the
+// thread's serial work between MMAs is time the tensor core idles.  Every
 // wait is bounded; an expired wait records GF2_ETIMEOUT in a device status
 // word and the CTA winds down (waits for its issued copies and MMAs, frees
 // its tensor memory) instead of hanging.
@@ -75,17 +80,17 @@ constexpr int PSTAGE_BYTES = PA_BYTES + PB_BYTES;
 constexpr int NUM_EPI_WARPS = 4;
 constexpr int MMA_WARP = 4;
 constexpr int TMA_WARP = 5;
-constexpr int AUNP_WARP0 = 6;      // four A unpackers, one per TMEM lane quarter
-constexpr int NUM_AUNP_WARPS = 4;
+constexpr int AUNP_WARP0 = 6;      // A unpackers: two per TMEM lane quarter (one per 128 K entries)
+constexpr int NUM_AUNP_WARPS = 8;
 constexpr int UNP_WARP0 = AUNP_WARP0 + NUM_AUNP_WARPS;         // B unpackers
 constexpr int NUM_UNP_WARPS = 12;
-constexpr int NTHREADS = (UNP_WARP0 + NUM_UNP_WARPS) * 32;     // 704
+constexpr int NTHREADS = (UNP_WARP0 + NUM_UNP_WARPS) * 32;     // 832
 constexpr int NUNP = NUM_UNP_WARPS * 32;                        // 384 = 2 * BN half rows
 constexpr int UNP_ARRIVALS = NUM_AUNP_WARPS + NUM_UNP_WARPS;    // arrivals that fill a stage
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long WAIT_LIMIT = 4000000000ull;        // clock64 cycles (~2 s)
 static_assert(NUNP == 2 * BN, "one half row of each 128-entry sub-tile per B unpacker thread");
-static_assert(AUNP_WARP0 % 4 == 2 && NUM_AUNP_WARPS == 4, "A unpackers cover the four lane quarters");
+static_assert(NUM_AUNP_WARPS == 8, "A unpackers: every lane quarter x both 128-entry halves");
 
 // tensor memory: accumulators at columns 0 and 256 (192 columns each), A
 // stages of 64 columns (256 K entries) at 192 and 448
@@ -426,9 +431,11 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         __syncwarp();
     } else if (warp >= AUNP_WARP0 && warp < UNP_WARP0) {
         // ------------------------------------------------------------ A unpackers
-        // thread = row of the A tile = its TMEM lane (warp w owns lanes 32 (w % 4) ..)
+        // thread = row of the A tile = its TMEM lane (warp w owns lanes 32 (w % 4) ..);
+        // warps 6-9 expand K entries 0-127 of the stage, warps 10-13 entries 128-255
         const int row = (warp & 3) * 32 + lane;
         const uint32_t tlane = (uint32_t)((warp & 3) * 32) << 16;
+        const int h = (warp - AUNP_WARP0) >> 2;
         int64_t q = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
@@ -440,20 +447,16 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             if (!warp_wait(empty_bar(s), (uint32_t)((q / STAGES) & 1) ^ 1u, P.status, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const uint64_t *pk = reinterpret_cast<const uint64_t *>(pbase + ps * PSTAGE_BYTES) + KW * row;
-            const uint32_t ta = tmem_base + tlane + a_col(s);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                // words beyond K arrive as zeros; bits beyond K in the last word are masked
-                const uint64_t w0 = pk[2 * h] & word_mask(kb * KW + 2 * h, T.l);
-                const uint64_t w1 = pk[2 * h + 1] & word_mask(kb * KW + 2 * h + 1, T.l);
-                uint32_t v[32];                        // K entries 128h + 4j .. 4j+3 in v[j]
-                expand_a((uint32_t)w0, v);
-                expand_a((uint32_t)(w0 >> 32), v + 8);
-                expand_a((uint32_t)w1, v + 16);
-                expand_a((uint32_t)(w1 >> 32), v + 24);
-                tmem_st32(ta + 32 * h, v);
-                tmem_wait_st();
-            }
+            // words beyond K arrive as zeros; bits beyond K in the last word are masked
+            const uint64_t w0 = pk[2 * h] & word_mask(kb * KW + 2 * h, T.l);
+            const uint64_t w1 = pk[2 * h + 1] & word_mask(kb * KW + 2 * h + 1, T.l);
+            uint32_t v[32];                            // K entries 128h + 4j .. 4j+3 in v[j]
+            expand_a((uint32_t)w0, v);
+            expand_a((uint32_t)(w0 >> 32), v + 8);
+            expand_a((uint32_t)w1, v + 16);
+            expand_a((uint32_t)(w1 >> 32), v + 24);
+            tmem_st32(tmem_base + tlane + a_col(s) + 32 * h, v);
+            tmem_wait_st();
             // the stores are complete: order them before the arrival the MMA
             // thread acquires, then hand the packed stage back
             tc_fence_before();
