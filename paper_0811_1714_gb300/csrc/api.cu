@@ -31,6 +31,21 @@ struct Arena {
 std::mutex g_arena_mu;
 std::map<std::pair<int, uintptr_t>, Arena> g_arenas;
 
+// One non-blocking side stream per device (created on first use), for
+// copies that overlap work on the caller's stream; ordered by events.
+cudaStream_t side_stream(int dev)
+{
+    static std::mutex mu;
+    static cudaStream_t st[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!st[dev] && cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        st[dev] = nullptr;
+    }
+    return st[dev];
+}
+
 int arena_get(cudaStream_t s, size_t bytes, void **out)
 {
     *out = nullptr;
@@ -235,7 +250,7 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
 
 // C = A B (or C ^= A B) for device matrices on the current device.
 int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan &p, int accumulate,
-               char *scratch, cudaStream_t s)
+               char *scratch, cudaStream_t s, cudaEvent_t b_ready = nullptr)
 {
     const int64_t m = p.m, l = p.l, n = p.n;
     if (m == 0 || n == 0) return GF2_OK;
@@ -247,28 +262,12 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     const bool tc = (p.base == GF2_BASE_TC_FP8);
     const uint64_t *Bsrc = B->data;
     int64_t ldBsrc = B->stride_words;
-    if (tc) {
-        uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
-        DMat T{Bt, n, l, p.ldBt};
-        DMat X{B->data, l, n, B->stride_words};
-        int rc = transpose_launch(T, X, s);
-        if (rc) return rc;
-        Bsrc = Bt;
-        ldBsrc = p.ldBt;
-    }
     const int d = p.depth;
-    if (d == 0)
-        return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
-                        m, l, n, 1, accumulate, s);
-
-    // top-down: the 8 additions of Algorithm 4 for every sub-problem of each
-    // level; two levels per launch while at least two remain (the middle
-    // level's operands then never leave registers)
-    int64_t cnt = 1;
-    for (int j = 1; j <= d;) {
-        const int step = (d - j + 1 >= 2) ? 2 : 1;
+    // the left factor's additions need nothing of B: with B still arriving
+    // (b_ready), they run first and B's work waits for the event
+    auto split_A = [&](int j, int step, int64_t cnt) {
         const int jt = j + step - 1;                       // level written
-        const int64_t Mp = p.M >> (j - 1), Lp = p.L >> (j - 1), Np = p.N >> (j - 1);
+        const int64_t Mp = p.M >> (j - 1), Lp = p.L >> (j - 1);
         SplitLaunch SA;
         SA.nparent = (int)cnt;
         SA.side = 0;
@@ -281,9 +280,41 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         }
         SA.out = reinterpret_cast<uint64_t *>(scratch + p.offA[jt]);
         SA.cld = p.ldA[jt]; SA.cbs = p.slabA[jt];
-        int rc = step == 2 ? sw_split2_launch(SA, s) : sw_split_launch(SA, s);
+        return step == 2 ? sw_split2_launch(SA, s) : sw_split_launch(SA, s);
+    };
+    if (d > 0) {
+        int64_t cnt = 1;
+        for (int j = 1; j <= d;) {
+            const int step = (d - j + 1 >= 2) ? 2 : 1;
+            int rc = split_A(j, step, cnt);
+            if (rc) return rc;
+            cnt *= (step == 2) ? 49 : 7;
+            j += step;
+        }
+    }
+    if (b_ready) GF2_CUDA_TRY(cudaStreamWaitEvent(s, b_ready, 0));
+    if (tc) {
+        uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
+        DMat T{Bt, n, l, p.ldBt};
+        DMat X{B->data, l, n, B->stride_words};
+        int rc = transpose_launch(T, X, s);
         if (rc) return rc;
+        Bsrc = Bt;
+        ldBsrc = p.ldBt;
+    }
+    if (d == 0)
+        return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
+                        m, l, n, 1, accumulate, s);
 
+    // top-down: the additions of Algorithm 4 (the left factor's above, the
+    // right factor's here) for every sub-problem of each level; two levels
+    // per launch while at least two remain (the middle level's operands then
+    // never leave registers)
+    int64_t cnt = 1;
+    for (int j = 1; j <= d;) {
+        const int step = (d - j + 1 >= 2) ? 2 : 1;
+        const int jt = j + step - 1;                       // level written
+        const int64_t Lp = p.L >> (j - 1), Np = p.N >> (j - 1);
         SplitLaunch SB;
         SB.nparent = (int)cnt;
         if (tc) {
@@ -307,7 +338,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         }
         SB.out = reinterpret_cast<uint64_t *>(scratch + p.offB[jt]);
         SB.cld = p.ldB[jt]; SB.cbs = p.slabB[jt];
-        rc = step == 2 ? sw_split2_launch(SB, s) : sw_split_launch(SB, s);
+        const int rc = step == 2 ? sw_split2_launch(SB, s) : sw_split_launch(SB, s);
         if (rc) return rc;
         cnt *= (step == 2) ? 49 : 7;
         j += step;
@@ -656,6 +687,25 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
     char *base = static_cast<char *>(scratch);
 
     gf2_mat dA = *A, dB = *B, dC = *C;
+    // with both factors on the host, B is copied on a side stream while the
+    // left factor's Strassen-Winograd additions run (they need only A)
+    cudaEvent_t b_ready = nullptr, s_ready = nullptr;
+    cudaStream_t sB = s;
+    if (hA && hB && m && l && n) {
+        sB = side_stream(dev);
+        if (!(sB && cudaEventCreateWithFlags(&b_ready, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&s_ready, cudaEventDisableTiming) == cudaSuccess)) {
+            cudaGetLastError();
+            if (b_ready) cudaEventDestroy(b_ready);
+            if (s_ready) cudaEventDestroy(s_ready);
+            b_ready = s_ready = nullptr;
+            sB = s;
+        }
+    }
+    struct EventGuard {
+        cudaEvent_t a, b;
+        ~EventGuard() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+    } guard{b_ready, s_ready};
     if (hA && m && l) {
         dA.data = reinterpret_cast<uint64_t *>(base + offA);
         dA.stride_words = even_up(words_of(l));
@@ -663,12 +713,19 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
         GF2_CUDA_TRY(cudaMemcpy2DAsync(dA.data, dA.stride_words * 8, A->data, A->stride_words * 8,
                                        words_of(l) * 8, m, cudaMemcpyHostToDevice, s));
     }
+    if (s_ready) {
+        // B's copy follows A's (they would share the link) and everything
+        // queued on s before it; it then overlaps A's additions
+        GF2_CUDA_TRY(cudaEventRecord(s_ready, s));
+        GF2_CUDA_TRY(cudaStreamWaitEvent(sB, s_ready, 0));
+    }
     if (hB && l && n) {
         dB.data = reinterpret_cast<uint64_t *>(base + offB);
         dB.stride_words = even_up(words_of(n));
         dB.device = dev;
         GF2_CUDA_TRY(cudaMemcpy2DAsync(dB.data, dB.stride_words * 8, B->data, B->stride_words * 8,
-                                       words_of(n) * 8, l, cudaMemcpyHostToDevice, s));
+                                       words_of(n) * 8, l, cudaMemcpyHostToDevice, sB));
+        if (b_ready) GF2_CUDA_TRY(cudaEventRecord(b_ready, sB));
     }
     if (hC && m && n) {
         dC.data = reinterpret_cast<uint64_t *>(base + offC);
@@ -679,7 +736,7 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
                                            words_of(n) * 8, m, cudaMemcpyHostToDevice, s));
     }
     if (!tuning) {
-        rc = mul_device(&dC, &dA, &dB, plans[0], o.accumulate, base, s);
+        rc = mul_device(&dC, &dA, &dB, plans[0], o.accumulate, base, s, b_ready);
         if (rc) return rc;
     } else {
         // time every candidate on these operands (each computes the same C)
@@ -688,6 +745,7 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
         GF2_CUDA_TRY(cudaEventCreate(&e1));
         size_t best = 0;
         float best_ms = 1e30f;
+        if (b_ready) GF2_CUDA_TRY(cudaStreamWaitEvent(s, b_ready, 0));
         for (size_t i = 0; i < plans.size(); ++i) {
             cudaEventRecord(e0, s);
             rc = mul_device(&dC, &dA, &dB, plans[i], 0, base, s);

@@ -265,6 +265,20 @@ def test_host_operands_through_the_abi():
     assert_same_bits(C, oracle.mul_packed(A, B, m, l, n), n, "host operands")
 
 
+@pytest.mark.parametrize("base,depth", [(g.GF2_BASE_M4RM, 2), (g.GF2_BASE_M4RM, 3), (g.GF2_BASE_TC_FP8, 2),
+                                        (g.GF2_BASE_M4RM, 0)])
+def test_host_operands_with_b_copied_beside_a_additions(base, depth):
+    """Both factors on the host: B's copy runs on a side stream while A's
+    Strassen-Winograd additions run; every call, back to back, with new
+    contents each time (a stale B would show)."""
+    m, l, n = 1300, 1500, 1100
+    for trial in range(3):
+        A, B = inputs(m, l, n, seeds=(60 + trial, 70 + trial))
+        C = np.full((m, synth.padded_stride(n)), 0xFFFF, np.uint64)
+        g.gf2_mul(g.mat(C, n), g.mat(A, l), g.mat(B, n), g.opts(base=base, depth=depth))
+        assert_same_bits(C, oracle.mul_packed(A, B, m, l, n), n, "host operands %d %d %d" % (base, depth, trial))
+
+
 def test_launch_count_grows():
     before = g.gf2_launch_count()
     gpu_mul(*inputs(64, 64, 64), 64, 64, 64, depth=0)
