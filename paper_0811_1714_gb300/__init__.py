@@ -44,6 +44,7 @@ GF2_HOST = -1
 GF2_BASE_AUTO = 0
 GF2_BASE_M4RM = 1
 GF2_BASE_TC_FP8 = 2
+GF2_BASE_TC_S8 = 3
 
 #: every symbol declared in include/gf2.h
 EXPORTS = (
@@ -369,7 +370,7 @@ def gf2_profile_name(family: int):
 
 
 PROFILE_FAMILIES = ("m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose", "random",
-                    "freivalds", "make_table", "batched")
+                    "freivalds", "make_table", "batched", "tc_s8")
 
 
 # ---- torch conveniences ----------------------------------------------------

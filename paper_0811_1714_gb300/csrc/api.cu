@@ -113,7 +113,7 @@ gf2_opts resolve(const gf2_opts *o)
 
 int check_opts(const gf2_opts &o)
 {
-    if (o.base < GF2_BASE_AUTO || o.base > GF2_BASE_TC_FP8) return GF2_EINVAL;
+    if (o.base < GF2_BASE_AUTO || o.base > GF2_BASE_TC_S8) return GF2_EINVAL;
     if (o.depth < -1 || o.depth > 8) return GF2_EINVAL;
     if (o.k < 0 || o.k > 10 || o.t < 0 || o.t > 16) return GF2_EINVAL;
     if (o.accumulate != 0 && o.accumulate != 1) return GF2_EINVAL;
@@ -154,7 +154,7 @@ int auto_depth(int64_t m, int64_t l, int64_t n, int base)
     // Recurse while every dimension of the sub-problems stays at or above the
     // cutoff (Section 5's c_o): each level saves 1/8 of the base-case work
     // and costs O(n^2) streaming additions.
-    const int64_t cutoff = (base == GF2_BASE_TC_FP8) ? 8192 : 4096;
+    const int64_t cutoff = (base == GF2_BASE_M4RM || base == GF2_BASE_AUTO) ? 4096 : 8192;
     int d = 0;
     int64_t mm = m, ll = l, nn = n;
     while (d < 6 && mm / 2 >= cutoff && ll / 2 >= cutoff && nn / 2 >= cutoff) {
@@ -179,7 +179,7 @@ int make_plan(int64_t m, int64_t l, int64_t n, const gf2_opts &o, Plan *p)
     p->N = d ? round_up(n, cq) : n;
     if (d && (p->M < 2 * rq / 2 || p->M / rq < 1)) return GF2_EUNSUPPORTED;
     p->k = o.k; p->t = o.t;
-    const bool tc = (p->base == GF2_BASE_TC_FP8);
+    const bool tc = (p->base == GF2_BASE_TC_FP8 || p->base == GF2_BASE_TC_S8);   // B held transposed
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
@@ -218,7 +218,7 @@ std::string plan_text(const Plan &p)
     char buf[512];
     snprintf(buf, sizeof buf,
              "base=%s depth=%d padded=%lldx%lldx%lld leaves=%lld leaf=%lldx%lldx%lld k=%d t=%d scratch=%zu",
-             p.base == GF2_BASE_TC_FP8 ? "tc_fp8" : "m4rm", p.depth, (long long)p.M, (long long)p.L,
+             p.base == GF2_BASE_TC_FP8 ? "tc_fp8" : (p.base == GF2_BASE_TC_S8 ? "tc_s8" : "m4rm"), p.depth, (long long)p.M, (long long)p.L,
              (long long)p.N, (long long)[&] { long long c = 1; for (int j = 0; j < p.depth; ++j) c *= 7; return c; }(),
              (long long)(p.M >> p.depth), (long long)(p.L >> p.depth), (long long)(p.N >> p.depth), p.k, p.t,
              p.bytes);
@@ -230,14 +230,14 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
              int64_t ldb, int64_t bsB, uint64_t *C, int64_t ldc, int64_t bsC, int64_t m, int64_t l,
              int64_t n, int batch, int accumulate, cudaStream_t s)
 {
-    if (p.base == GF2_BASE_TC_FP8) {
+    if (p.base == GF2_BASE_TC_FP8 || p.base == GF2_BASE_TC_S8) {
         TcLaunch L;
         L.A = A; L.lda = lda; L.bsA = bsA;
         L.Bt = B; L.ldb = ldb; L.bsB = bsB;
         L.C = C; L.ldc = ldc; L.bsC = bsC;
         L.m = m; L.l = l; L.n = n; L.batch = batch; L.accumulate = accumulate;
         L.status = nullptr;
-        return tc_fp8_launch(L, s);
+        return p.base == GF2_BASE_TC_S8 ? tc_s8_launch(L, s) : tc_fp8_launch(L, s);
     }
     M4rmLaunch L;
     L.A = A; L.lda = lda; L.bsA = bsA;
@@ -259,7 +259,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         GF2_CUDA_TRY(cudaMemset2DAsync(C->data, C->stride_words * 8, 0, words_of(n) * 8, m, s));
         return GF2_OK;
     }
-    const bool tc = (p.base == GF2_BASE_TC_FP8);
+    const bool tc = (p.base == GF2_BASE_TC_FP8 || p.base == GF2_BASE_TC_S8);
     const uint64_t *Bsrc = B->data;
     int64_t ldBsrc = B->stride_words;
     const int d = p.depth;
@@ -575,7 +575,7 @@ int gf2_describe_plan(int64_t m, int64_t l, int64_t n, const gf2_opts *opts, cha
     rc = make_plan(m, l, n, eff, &p);
     if (rc) return rc;
     std::string t = plan_text(p);
-    if (p.base != GF2_BASE_TC_FP8 && m > 0 && n > 0) {
+    if (p.base == GF2_BASE_M4RM && m > 0 && n > 0) {
         int k = o.k, tt = o.t, bm = 0, ks = 0;
         const int d = p.depth;
         int batch = 1;
@@ -644,7 +644,7 @@ int gf2_profile_read(int32_t family, double *ms, int64_t *launches)
 const char *gf2_profile_name(int32_t family)
 {
     static const char *names[PF_COUNT] = {"m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose",
-                                          "random", "freivalds", "make_table", "batched"};
+                                          "random", "freivalds", "make_table", "batched", "tc_s8"};
     if (family < 0 || family >= PF_COUNT) return nullptr;
     return names[family];
 }

@@ -40,7 +40,7 @@ void note_launch(int n = 1);
 
 // Kernel families for the device-time accounting of gf2_profile_*.
 enum ProfFamily { PF_M4RM = 0, PF_TC, PF_SPLIT, PF_COMBINE, PF_TRANSPOSE, PF_RANDOM, PF_MATVEC,
-                  PF_TABLE, PF_BATCHED, PF_COUNT };
+                  PF_TABLE, PF_BATCHED, PF_TC_S8, PF_COUNT };
 
 // Brackets the launches made during its lifetime with CUDA events on `s`
 // when accounting is on.
@@ -131,6 +131,7 @@ struct TcLaunch {
     unsigned int *status;                    // device word for timeouts (may be null)
 };
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
+int tc_s8_launch(const TcLaunch &L, cudaStream_t s);
 
 // Autotuner cache (tune.cu): text signature -> text choice.
 bool tune_get(const std::string &key, std::string *value);
