@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--p", type=float, default=0.5, help="density of one bits (square workload)")
     ap.add_argument("--paths", default="m4rm,tc_fp8,tc_s8", help="base cases to time")
     ap.add_argument("--depth", type=int, default=-1)
     ap.add_argument("--k", type=int, default=0)
@@ -219,8 +220,8 @@ def run_ours(args, rank, world, local_rank):
     B = g.empty(l, n)
     C = g.empty(m, n)
     MA, MB, MC = g.mat(A, l), g.mat(B, n), g.mat(C, n)
-    g.gf2_random(MA, 1 + 100 * rank)
-    g.gf2_random(MB, 2 + 100 * rank)
+    g.gf2_random(MA, 1 + 100 * rank, args.p)
+    g.gf2_random(MB, 2 + 100 * rank, args.p)
     torch.cuda.synchronize()
     peaks, peak_kind = load_peaks()
 
@@ -314,8 +315,8 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64-packed-bits" if head == "m4rm" else "fp8e4m3-0/1",
-        "data": "synthetic: SplitMix64 Bernoulli(1/2) bits, seeds 1/2 (+100*rank)",
-        "config": {"workload": "square C=A*B over GF(2), m=l=n=%d" % n, "m": m, "l": l, "n": n,
+        "data": "synthetic: SplitMix64 Bernoulli(%g) bits, seeds 1/2 (+100*rank)" % args.p,
+        "config": {"workload": "square C=A*B over GF(2), m=l=n=%d" % n, "m": m, "l": l, "n": n, "p": args.p,
                    "base": head, "depth": H["depth"], "plan": H["plan"],
                    "parallelism": "independent product per GPU" if world > 1 else "single GPU",
                    "l2": "inputs 2 x %d MiB + output %d MiB exceed the 129 MB L2" % (
