@@ -27,6 +27,10 @@
  *  - the caller owns every gf2_mat; the library owns only its scratch arenas
  *    (one per device and stream, grown on demand, released by
  *    gf2_release_scratch) and its autotuning cache;
+ *  - calls may come from several host threads, on the same stream or on
+ *    different ones: a call holds its stream's arena until it has queued
+ *    all work that uses it (gf2_mul_noalloc's fixed buffer excepted, see
+ *    there);
  *  - a matrix with device >= 0 lives in that device's global memory; with
  *    device == GF2_HOST it lives in host memory (pinned memory gives full
  *    copy speed).  gf2_mul accepts host operands and then copies them

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -24,12 +25,18 @@ using namespace gf2;
 namespace {
 
 // ---------------------------------------------------------------- arenas
+// One arena per (device, stream).  A caller holds the arena's mutex from
+// arena_get until it has queued all work that uses the arena, so another
+// host thread on the same stream can neither grow (free) it nor hand the same
+// bytes out in between.
 struct Arena {
+    std::mutex mu;
     void *ptr = nullptr;
     size_t bytes = 0;
+    ~Arena() { if (ptr) cudaFree(ptr); }
 };
-std::mutex g_arena_mu;
-std::map<std::pair<int, uintptr_t>, Arena> g_arenas;
+std::mutex g_arena_mu;   // guards the map, not the arenas
+std::map<std::pair<int, uintptr_t>, std::shared_ptr<Arena>> g_arenas;
 
 // One non-blocking side stream per device (created on first use), for
 // copies that overlap work on the caller's stream; ordered by events.
@@ -46,14 +53,26 @@ cudaStream_t side_stream(int dev)
     return st[dev];
 }
 
-int arena_get(cudaStream_t s, size_t bytes, void **out)
+struct ArenaHold {
+    std::shared_ptr<Arena> arena;
+    std::unique_lock<std::mutex> lock;
+};
+
+int arena_get(cudaStream_t s, size_t bytes, void **out, ArenaHold *hold)
 {
     *out = nullptr;
     if (bytes == 0) return GF2_OK;
     int dev = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(g_arena_mu);
-    Arena &a = g_arenas[{dev, reinterpret_cast<uintptr_t>(s)}];
+    std::shared_ptr<Arena> ap;
+    {
+        std::lock_guard<std::mutex> lk(g_arena_mu);
+        auto &slot = g_arenas[{dev, reinterpret_cast<uintptr_t>(s)}];
+        if (!slot) slot = std::make_shared<Arena>();
+        ap = slot;
+    }
+    std::unique_lock<std::mutex> lk(ap->mu);
+    Arena &a = *ap;
     if (a.bytes < bytes) {
         if (a.ptr) {
             // earlier work queued on this stream may still use the old arena
@@ -71,6 +90,8 @@ int arena_get(cudaStream_t s, size_t bytes, void **out)
         a.bytes = want;
     }
     *out = a.ptr;
+    hold->arena = std::move(ap);
+    hold->lock = std::move(lk);
     return GF2_OK;
 }
 
@@ -593,7 +614,8 @@ int gf2_reserve_scratch(int64_t bytes, void *stream)
 {
     if (bytes < 0) return GF2_EINVAL;
     void *p = nullptr;
-    return arena_get(static_cast<cudaStream_t>(stream), (size_t)bytes, &p);
+    ArenaHold hold;
+    return arena_get(static_cast<cudaStream_t>(stream), (size_t)bytes, &p, &hold);
 }
 
 int gf2_release_scratch(void)
@@ -602,16 +624,23 @@ int gf2_release_scratch(void)
     GF2_CUDA_TRY(cudaGetDevice(&dev));
     gf2::batched_release();
     gf2::tc_batched_release();
-    std::lock_guard<std::mutex> lk(g_arena_mu);
-    GF2_CUDA_TRY(cudaDeviceSynchronize());
-    for (auto it = g_arenas.begin(); it != g_arenas.end();) {
-        if (it->first.first == dev) {
-            if (it->second.ptr) cudaFree(it->second.ptr);
-            it = g_arenas.erase(it);
-        } else {
-            ++it;
+    std::vector<std::shared_ptr<Arena>> gone;
+    {
+        std::lock_guard<std::mutex> lk(g_arena_mu);
+        for (auto it = g_arenas.begin(); it != g_arenas.end();) {
+            if (it->first.first == dev) {
+                gone.push_back(it->second);
+                it = g_arenas.erase(it);
+            } else {
+                ++it;
+            }
         }
     }
+    // wait for callers still queueing work into these arenas, then for the
+    // device; an arena still held elsewhere is freed when its holder drops it
+    for (auto &a : gone) std::lock_guard<std::mutex> wait(a->mu);
+    GF2_CUDA_TRY(cudaDeviceSynchronize());
+    gone.clear();
     return GF2_OK;
 }
 
@@ -683,7 +712,8 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
     if (hB) { offB = total; total += (staged_bytes(B) + 255) & ~(size_t)255; }
     if (hC) { offC = total; total += (staged_bytes(C) + 255) & ~(size_t)255; }
     void *scratch = nullptr;
-    if ((rc = arena_get(s, total, &scratch))) return rc;
+    ArenaHold hold;
+    if ((rc = arena_get(s, total, &scratch, &hold))) return rc;
     char *base = static_cast<char *>(scratch);
 
     gf2_mat dA = *A, dB = *B, dC = *C;
@@ -934,7 +964,8 @@ int gf2_freivalds(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, uint64_t
     const size_t oY3 = take((size_t)m * 8);
     const size_t oCnt = take(8);
     void *scr = nullptr;
-    if ((rc = arena_get(s, off, &scr))) return rc;
+    ArenaHold hold;
+    if ((rc = arena_get(s, off, &scr, &hold))) return rc;
     char *b = static_cast<char *>(scr);
     uint64_t *X = reinterpret_cast<uint64_t *>(b + oX), *XT = reinterpret_cast<uint64_t *>(b + oXT);
     uint64_t *Y1 = reinterpret_cast<uint64_t *>(b + oY1), *Y1T = reinterpret_cast<uint64_t *>(b + oY1T);
