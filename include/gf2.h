@@ -81,7 +81,13 @@ typedef struct gf2_opts {
     int32_t k;             /* M4RM bits per table (Section 3.1 "k"): 0 = auto, else 4..10 */
     int32_t t;             /* M4RM tables per pass (Section 3.3 "t"): 0 = auto            */
     int32_t accumulate;    /* 0: C = A B;  1: C ^= A B                                    */
-    int32_t reserved[3];   /* must be 0                                                   */
+    int32_t peel;          /* sizes that do not halve evenly (Section 4): 0 = virtual
+                              zero padding; 1 = peeling: Strassen-Winograd on the largest
+                              evenly halving core, the leftover rows, columns and K
+                              entries by base-case products (device operands); -1 = the
+                              autotuner times both on the first call for a shape
+                              (gf2_default_opts; padding where it does not tune)       */
+    int32_t reserved[2];   /* must be 0                                                   */
 } gf2_opts;
 
 /* Fill *opts with the defaults (everything automatic, C = A B). */

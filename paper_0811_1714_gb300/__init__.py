@@ -81,14 +81,14 @@ class Mat(ctypes.Structure):
 class Opts(ctypes.Structure):
     """``gf2_opts``."""
     _fields_ = [("base", ctypes.c_int32), ("depth", ctypes.c_int32), ("k", ctypes.c_int32),
-                ("t", ctypes.c_int32), ("accumulate", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("t", ctypes.c_int32), ("accumulate", ctypes.c_int32), ("peel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 def opts(base: int = GF2_BASE_AUTO, depth: int = -1, k: int = 0, t: int = 0,
-         accumulate: int = 0) -> Opts:
+         accumulate: int = 0, peel: int = -1) -> Opts:
     o = Opts()
-    o.base, o.depth, o.k, o.t, o.accumulate = base, depth, k, t, accumulate
+    o.base, o.depth, o.k, o.t, o.accumulate, o.peel = base, depth, k, t, accumulate, peel
     return o
 
 

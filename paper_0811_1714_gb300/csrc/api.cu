@@ -138,7 +138,8 @@ int check_opts(const gf2_opts &o)
     if (o.depth < -1 || o.depth > 8) return GF2_EINVAL;
     if (o.k < 0 || o.k > 10 || o.t < 0 || o.t > 16) return GF2_EINVAL;
     if (o.accumulate != 0 && o.accumulate != 1) return GF2_EINVAL;
-    if (o.reserved[0] || o.reserved[1] || o.reserved[2]) return GF2_EINVAL;
+    if (o.peel < -1 || o.peel > 1) return GF2_EINVAL;
+    if (o.reserved[0] || o.reserved[1]) return GF2_EINVAL;
     if (o.k > 0 && o.t > 0 && !m4rm_supported(o.k, o.t)) return GF2_EUNSUPPORTED;
     return GF2_OK;
 }
@@ -399,6 +400,82 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     return GF2_OK;
 }
 
+// ---------------------------------------------------------------- peeling
+// Section 4's alternative to padding for sizes that do not halve evenly:
+// Strassen-Winograd on the largest core whose rows are a multiple of 2^d and
+// whose column counts are multiples of 128 * 2^d (the quadrants of every
+// level then start on 16-byte boundaries), and the leftovers by base-case
+// products on views of the same matrices:
+//   C[0:M', 0:N']  = A[0:M', 0:L'] B[0:L', 0:N']   (recursion)
+//                  ^ A[0:M', L':l] B[L':l, 0:N']   (leftover K entries)
+//   C[0:M', N':n]  = A[0:M', :] B[:, N':n]          (leftover columns)
+//   C[M':m, :]     = A[M':m, :] B                   (leftover rows)
+// The paper peels one row or column per level; peeling the whole remainder
+// once, at the top, gives the same product with fewer and larger launches.
+struct PeelCore {
+    int base, depth;
+    int64_t M1, L1, N1;       // the core; all zero when nothing is peeled
+};
+
+PeelCore peel_core(int64_t m, int64_t l, int64_t n, const gf2_opts &o)
+{
+    PeelCore c;
+    c.base = o.base == GF2_BASE_AUTO ? GF2_BASE_M4RM : o.base;
+    c.depth = o.depth < 0 ? auto_depth(m, l, n, c.base) : o.depth;
+    const int64_t rq = (int64_t)1 << c.depth, cq = (int64_t)128 << c.depth;
+    c.M1 = m / rq * rq; c.L1 = l / cq * cq; c.N1 = n / cq * cq;
+    if (c.depth == 0 || c.M1 == 0 || c.L1 == 0 || c.N1 == 0 || (c.M1 == m && c.L1 == l && c.N1 == n))
+        c.M1 = c.L1 = c.N1 = 0;
+    return c;
+}
+
+int mul_peeled(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts &o, void *stream)
+{
+    const int64_t m = A->rows, l = A->cols, n = B->cols;
+    const PeelCore pc = peel_core(m, l, n, o);
+    const int base = pc.base, d = pc.depth;
+    const int64_t M1 = pc.M1, L1 = pc.L1, N1 = pc.N1;
+    gf2_opts plain = o;
+    plain.peel = 0;
+    plain.base = base;
+    if (M1 == 0) {
+        plain.depth = d;
+        return gf2_mul(C, A, B, &plain, stream);      // nothing to peel, or no core
+    }
+    auto view = [](const gf2_mat *X, int64_t r0, int64_t c0, int64_t rows, int64_t cols) {
+        gf2_mat v = *X;
+        v.data = X->data + r0 * X->stride_words + c0 / 64;   // c0 is a multiple of 128
+        v.rows = rows;
+        v.cols = cols;
+        return v;
+    };
+    int rc;
+    // core
+    {
+        gf2_mat a = view(A, 0, 0, M1, L1), b = view(B, 0, 0, L1, N1), c = view(C, 0, 0, M1, N1);
+        gf2_opts oc = plain;
+        oc.depth = d;
+        if ((rc = gf2_mul(&c, &a, &b, &oc, stream))) return rc;
+    }
+    gf2_opts ob = plain;
+    ob.depth = 0;
+    if (L1 < l) {
+        gf2_mat a = view(A, 0, L1, M1, l - L1), b = view(B, L1, 0, l - L1, N1), c = view(C, 0, 0, M1, N1);
+        gf2_opts oa = ob;
+        oa.accumulate = 1;
+        if ((rc = gf2_mul(&c, &a, &b, &oa, stream))) return rc;
+    }
+    if (N1 < n) {
+        gf2_mat a = view(A, 0, 0, M1, l), b = view(B, 0, N1, l, n - N1), c = view(C, 0, N1, M1, n - N1);
+        if ((rc = gf2_mul(&c, &a, &b, &ob, stream))) return rc;
+    }
+    if (M1 < m) {
+        gf2_mat a = view(A, M1, 0, m - M1, l), c = view(C, M1, 0, m - M1, n);
+        if ((rc = gf2_mul(&c, &a, B, &ob, stream))) return rc;
+    }
+    return GF2_OK;
+}
+
 // ---------------------------------------------------------------- autotuning
 // gf2_mul with an automatic base case and/or depth on a large product
 // (m*l*n >= 2^36) asks the autotuner: a cached choice for this shape, or,
@@ -473,6 +550,44 @@ size_t staged_bytes(const gf2_mat *M)
     return (size_t)(M->rows * even_up(words_of(M->cols))) * 8;
 }
 
+// Padding or peeling for this shape (opts.peel == -1): 0 = pad, 1 = peel,
+// 2 = C already holds A B (computed while timing), or a negative status.
+// Where the autotuner does not run (small products, accumulate, tuning
+// off, or nothing to peel) the answer is padding; otherwise the first call
+// for a shape times both on the caller's operands and caches the faster.
+int choose_peel(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts &o, void *stream)
+{
+    const int64_t m = A->rows, l = A->cols, n = B->cols;
+    const double vol = (double)m * (double)l * (double)n;
+    if (o.accumulate || vol < 68719476736.0 || !autotune_enabled()) return 0;
+    if (!peel_core(m, l, n, o).M1) return 0;
+    const std::string key = "peel|" + tune_key(m, l, n, o);
+    std::string v;
+    if (tune_get(key, &v)) return v == "peel" ? 1 : 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    gf2_opts op = o, oq = o;
+    op.peel = 0;
+    oq.peel = 1;
+    int rc = gf2_mul(C, A, B, &op, stream);              // warms (and tunes) the padded plan
+    if (rc) return rc;
+    cudaEvent_t e[3];
+    for (auto &ev : e) GF2_CUDA_TRY(cudaEventCreate(&ev));
+    float t_pad = 0.f, t_peel = 0.f;
+    cudaEventRecord(e[0], s);
+    rc = gf2_mul(C, A, B, &op, stream);
+    cudaEventRecord(e[1], s);
+    if (!rc) rc = mul_peeled(C, A, B, oq, stream);
+    cudaEventRecord(e[2], s);
+    if (!rc && cudaEventSynchronize(e[2]) == cudaSuccess) {
+        cudaEventElapsedTime(&t_pad, e[0], e[1]);
+        cudaEventElapsedTime(&t_peel, e[1], e[2]);
+    }
+    for (auto &ev : e) cudaEventDestroy(ev);
+    if (rc) return rc;
+    tune_put(key, t_peel < t_pad ? "peel" : "pad");
+    return 2;
+}
+
 }  // namespace
 
 namespace gf2 {
@@ -515,6 +630,7 @@ void gf2_default_opts(gf2_opts *o)
     memset(o, 0, sizeof(*o));
     o->base = GF2_BASE_AUTO;
     o->depth = -1;
+    o->peel = -1;
 }
 
 const char *gf2_strerror(int status)
@@ -591,11 +707,31 @@ int gf2_describe_plan(int64_t m, int64_t l, int64_t n, const gf2_opts *opts, cha
     std::vector<gf2_opts> cands;
     std::string key;
     gf2_opts eff = o;
-    if (!wants_tuning(m, l, n, o, &cands, &key)) eff = cands[0];
+    std::string peeled;
+    int policy = o.peel;
+    if (policy == -1) {      // the autotuner's cached choice for this shape, else padding
+        std::string v;
+        policy = (tune_get("peel|" + tune_key(m, l, n, o), &v) && v == "peel") ? 1 : 0;
+    }
+    if (policy == 1) {
+        const PeelCore pc = peel_core(m, l, n, o);
+        eff.peel = 0;
+        eff.base = pc.base;
+        eff.depth = pc.depth;
+        if (pc.M1) {
+            char pb[160];
+            snprintf(pb, sizeof pb, " peel core=%lldx%lldx%lld leftover rows=%lld cols=%lld k=%lld",
+                     (long long)pc.M1, (long long)pc.L1, (long long)pc.N1, (long long)(m - pc.M1),
+                     (long long)(n - pc.N1), (long long)(l - pc.L1));
+            peeled = pb;
+            m = pc.M1; l = pc.L1; n = pc.N1;              // the recursion's plan is the core's
+        }
+    }
+    if (!wants_tuning(m, l, n, eff, &cands, &key)) eff = cands[0];
     Plan p;
     rc = make_plan(m, l, n, eff, &p);
     if (rc) return rc;
-    std::string t = plan_text(p);
+    std::string t = plan_text(p) + peeled;
     if (p.base == GF2_BASE_M4RM && m > 0 && n > 0) {
         int k = o.k, tt = o.t, bm = 0, ks = 0;
         const int d = p.depth;
@@ -694,6 +830,13 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
         if (M->device != GF2_HOST && M->device != dev && M->rows && M->cols) return GF2_EINVAL;
 
     const int64_t m = A->rows, l = A->cols, n = B->cols;
+    if (o.peel && A->device != GF2_HOST && B->device != GF2_HOST && C->device != GF2_HOST) {
+        if (o.peel == 1) return mul_peeled(C, A, B, o, stream);
+        const int choice = choose_peel(C, A, B, o, stream);
+        if (choice < 0) return choice;                   // an error
+        if (choice == 2) return GF2_OK;                  // C computed while choosing
+        if (choice == 1) return mul_peeled(C, A, B, o, stream);
+    }
     // candidate plans: one, or several when the autotuner picks base / depth
     std::vector<gf2_opts> cands;
     std::string tkey;

@@ -101,6 +101,21 @@ def test_argument_checks(lib):
     o = g.opts()
     o.reserved[1] = 1
     assert rc_of(g.gf2_mul, C, A, B, o) == g.GF2_EINVAL
+    assert rc_of(g.gf2_mul, C, A, B, g.opts(peel=2)) == g.GF2_EINVAL
+
+
+def test_plan_with_peeling(lib):
+    """Peeling (Section 4): the recursion runs on the largest core whose rows
+    are a multiple of 2^d and whose columns are multiples of 128 * 2^d."""
+    p = g.gf2_describe_plan(20000, 12000, 28000, g.opts(depth=2, base=g.GF2_BASE_M4RM, peel=1))
+    assert "peel core=20000x11776x27648" in p and "padded=20000x11776x27648" in p, p
+    assert "leftover rows=0 cols=352 k=224" in p, p
+    # sizes that already halve evenly: nothing to peel
+    q = g.gf2_describe_plan(4096, 4096, 4096, g.opts(depth=2, peel=1))
+    assert "peel" not in q and "depth=2" in q
+    # no core at this depth: the product runs as requested without peeling
+    r = g.gf2_describe_plan(300, 100, 300, g.opts(depth=1, peel=1))
+    assert "peel" not in r
 
 
 def test_plan_padding_and_scratch(lib):
