@@ -450,13 +450,23 @@ void m4rm_pick(int64_t m, int64_t l, int64_t n, int batch, int *k, int *t, int *
 {
     const int sms = sm_count();
     const int64_t tn = (words_of(n) + TILE_WORDS - 1) / TILE_WORDS;
+    // Shared-memory wavefronts per bit of K of one tile (table-row reads,
+    // table build, A-index and staged-B reads), counted for the default
+    // (k, t) of each height: 2048 rows k=8 t=4, 1024 rows k=8 t=4, 256 rows
+    // k=6 t=8, 64 rows k=4 t=8.  Among the heights that give every SM two
+    // CTAs, take the one that minimises tiles x cost: a ragged m (2111
+    // rows, say) is cheaper in 256-row tiles than in two 2048-row tiles.
     const int bms[4] = {2048, 1024, 256, 64};
-    int b = 1024;
+    const double cost[4] = {316.0, 180.0, 56.8, 22.5};
+    int b = 64;
+    double best = 1e300;
     for (int i = 0; i < 4; ++i) {
-        b = bms[i];
-        if (b == 2048 && m <= 1024) continue;       // the tensor-memory half would hold no rows
-        const int64_t ctas = (int64_t)batch * tn * ((m + b - 1) / b);
-        if (ctas >= 2 * sms) break;
+        if (bms[i] == 2048 && m <= 1024) continue;  // the tensor-memory half would hold no rows
+        const int64_t tm = (m + bms[i] - 1) / bms[i];
+        const int64_t ctas = (int64_t)batch * tn * tm;
+        if (ctas < 2 * sms) continue;
+        const double c = (double)tm * cost[i];
+        if (c < best) { best = c; b = bms[i]; }
     }
     int kk = (b >= 1024) ? 8 : (b == 256 ? 6 : 4);
     int tt = (b >= 1024) ? 4 : 8;

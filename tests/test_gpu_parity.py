@@ -100,7 +100,7 @@ def test_m4rm_tall_tiles_with_tensor_memory_half(accumulate):
     """2048-row tiles (one half in registers, one in tensor memory): rows
     ragged at the tile end and checked across the half boundary (row 1024),
     columns ragged in the last tile, K not a multiple of the 32-bit pass."""
-    m, l, n = 2 * 2048 + 77, 333, 159 * 1024 + 200
+    m, l, n = 2 * 2048 + 1500, 333, 159 * 1024 + 200
     plan = g.gf2_describe_plan(m, l, n, g.opts(base=g.GF2_BASE_M4RM, depth=0))
     assert "tile_rows=2048" in plan, plan
     A, B = inputs(m, l, n, seeds=(41, 42))
@@ -113,7 +113,7 @@ def test_m4rm_tall_tiles_with_tensor_memory_half(accumulate):
               g.opts(base=g.GF2_BASE_M4RM, depth=0, accumulate=accumulate))
     g.gf2_device_status()
     got = to_host(Cd)
-    for r0, r1 in ((0, 40), (1000, 1050), (2030, 2080), (3060, 3090), (4096, m)):
+    for r0, r1 in ((0, 40), (1000, 1050), (2030, 2080), (3060, 3090), (5100, 5150), (5560, m)):
         ref = oracle.mul_packed(np.ascontiguousarray(A[r0:r1]), B, r1 - r0, l, n)
         if accumulate:
             ref = ref ^ C0[r0:r1]
