@@ -42,15 +42,17 @@ def check_product(m, l, n, base, p=0.5, seeds=(1, 2), blocks=4, depth=-1):
     g.gf2_device_status()
     assert g.gf2_freivalds(MC, MA, MB, synth.SEED_FREIVALDS) == 0, plan
     rng = np.random.default_rng(m ^ (l << 1) ^ (n << 2) ^ base)
-    for _ in range(blocks):
-        r0 = int(rng.integers(0, m - 64))
-        c0 = 64 * int(rng.integers(0, (n - 64) // 64))
-        Ar = synth.random_packed(64, l, seeds[0], p, row0=r0)
-        Bc = synth.random_packed_cols(l, n, seeds[1], c0, c0 + 64, p)
-        ref = oracle.mul_packed(Ar, Bc, 64, l, 64)
-        got = C[r0:r0 + 64, c0 // 64:c0 // 64 + 1]
+    # one 1024 x 1024 block, then smaller 64 x 64 ones, all drawn on the host
+    for i in range(blocks):
+        h = 1024 if i == 0 else 64
+        r0 = int(rng.integers(0, m - h))
+        c0 = 64 * int(rng.integers(0, (n - h) // 64))
+        Ar = synth.random_packed(h, l, seeds[0], p, row0=r0)
+        Bc = synth.random_packed_cols(l, n, seeds[1], c0, c0 + h, p)
+        ref = oracle.mul_packed(Ar, Bc, h, l, h)
+        got = C[r0:r0 + h, c0 // 64:c0 // 64 + h // 64]
         got = np.ascontiguousarray(to_host(got.contiguous()))
-        assert np.array_equal(valid_words(got, 64), valid_words(ref, 64)), (plan, r0, c0)
+        assert np.array_equal(valid_words(got, h), valid_words(ref, h)), (plan, r0, c0, h)
     del A, B, C
     torch.cuda.empty_cache()
 
