@@ -426,14 +426,39 @@ def run_batched(args, rank, world, local_rank):
 
     g.gf2_profile_enable(True)
     ms_local, launches = timed(None)
+    k_ms, k_n = g.gf2_profile_read(g.PROFILE_FAMILIES.index("batched"))
     g.gf2_profile_enable(False)
     bad = sampled_bad(5)
+    peaks, peak_kind = load_peaks()
+    vname = g.gf2_batched_variant_name(variant)
+    kbits = int(vname.split("-k")[1][0]) if "-k" in vname else (int(vname[1]) if vname.startswith("k") else 8)
+    # table-row reads of the k-bit tables: m*l*n / (8k) bytes per product
+    rl = None
+    if k_n:
+        per_launch_ms = k_ms / k_n
+        smem_bytes = sum(m * l * n for m, l, n in dims) / (8.0 * kbits)
+        achieved = smem_bytes / (per_launch_ms * 1e-3) / 1e9
+        peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+        rl = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+              "traffic": None, "kernel_ms_per_launch": per_launch_ms,
+              "peak_note": "152 SMs x 128 B/clk x %.0f MHz (shared-memory bandwidth)" % peaks.get("sm_max_mhz", 2070.0),
+              "work_note": "table-row reads of k=%d tables, sum of m*l*n/(8k) over the 4096 products" % kbits}
     ms, ops_all, value = aggregate(ms_local, ops)
     # the same batch on the tensor-core base case: one batched transpose and
     # one persistent tensor-core launch per step
+    g.gf2_profile_enable(True)
     tc_ms_local, tc_launches = timed(g.opts(base=g.GF2_BASE_TC_FP8, depth=0))
+    t_ms, t_n = g.gf2_profile_read(g.PROFILE_FAMILIES.index("tc_fp8"))
+    g.gf2_profile_enable(False)
     tc_ms, _, tc_value = aggregate(tc_ms_local, ops)
-    tc = {"ms_per_step": tc_ms, "value": tc_value, "gpu_launches": tc_launches,
+    tc_rl = None
+    if t_n:
+        flops = sum(2.0 * m * l * n for m, l, n in dims)
+        ach = flops / (t_ms / t_n * 1e-3) / 1e12
+        pk = 2.0 * peaks["bf16_tflops"]
+        tc_rl = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                 "traffic": None, "peak_note": "2 x bf16 burst of %s peaks (nominal fp8/bf16 ratio)" % peak_kind}
+    tc = {"ms_per_step": tc_ms, "value": tc_value, "gpu_launches": tc_launches, "roofline": tc_rl,
           "graph": "batched transpose of every B + one persistent tensor-core kernel",
           "freivalds_sampled_products_failed": sampled_bad(9)}
     ops = ops_all
@@ -444,7 +469,7 @@ def run_batched(args, rank, world, local_rank):
         "dtype": "u64-packed-bits", "data": "synthetic: SplitMix64 bits, dims log-uniform [64, 2048] seed 42",
         "config": {"workload": "4096 batched products, m,l,n log-uniform in [64, 2048]",
                    "variant": g.gf2_batched_variant_name(variant), "total_bit_ops": ops},
-        "gpu_launches": launches,
+        "gpu_launches": launches, "roofline": rl,
         "graph": "each step replays one CUDA graph: counter reset + one persistent kernel",
         "verified": {"freivalds_sampled_products_failed": bad},
         "tc_fp8_base": tc,

@@ -624,6 +624,7 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
             g_graphs.splice(g_graphs.begin(), g_graphs, it);       // most recently used
             if (chosen) *chosen = g_graphs.front().variant;
             if (g_graphs.front().ntiles == 0) return GF2_OK;
+            ProfScope ps(PF_BATCHED, s);
             GF2_CUDA_TRY(cudaGraphLaunch(g_graphs.front().exec, s));
             note_launch();
             return GF2_OK;
@@ -684,7 +685,10 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
         kp.kernelParams = args;
         if (cudaGraphAddKernelNode(&nker, e.graph, &nmem, 1, &kp) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
         if (cudaGraphInstantiate(&e.exec, e.graph, 0) != cudaSuccess) { free_entry(e); cudaGetLastError(); return GF2_ECUDA; }
-        if (cudaGraphLaunch(e.exec, s) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        {
+            ProfScope ps(PF_BATCHED, s);
+            if (cudaGraphLaunch(e.exec, s) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        }
         note_launch();
     }
     g_graphs.push_front(std::move(e));
