@@ -164,8 +164,9 @@ struct Plan {
     size_t offA[kMaxDepth + 1], offB[kMaxDepth + 1], offP[kMaxDepth + 1];
     int64_t ldA[kMaxDepth + 1], ldB[kMaxDepth + 1], ldP[kMaxDepth + 1];
     int64_t slabA[kMaxDepth + 1], slabB[kMaxDepth + 1], slabP[kMaxDepth + 1];
-    size_t offBt;        // transposed B (tensor-core base, depth 0 or top of the split)
-    int64_t ldBt;
+    size_t offBt;        // transposed B (tensor-core base, depth 0 or top of the split;
+    int64_t ldBt;        // the cubic form: 64 rows)
+    bool cubic;          // depth 0, at most 64 columns: the cubic product of Section 2.3
     size_t bytes;        // total device scratch (without host staging)
 };
 
@@ -231,6 +232,14 @@ int make_plan(int64_t m, int64_t l, int64_t n, const gf2_opts &o, Plan *p)
         p->ldBt = even_up(words_of(l));
         p->offBt = take((size_t)(n * p->ldBt) * 8);
     }
+    // a right factor of at most 64 columns (Section 2.3, the paper's choice
+    // over M4RM there): one word of C per row, from B's columns as rows
+    p->cubic = (p->base == GF2_BASE_M4RM && d == 0 && o.k == 0 && o.t == 0 && m > 0 && l > 0 && n > 0 &&
+                n <= 64);
+    if (p->cubic) {
+        p->ldBt = even_up(words_of(l));
+        p->offBt = take((size_t)(64 * p->ldBt) * 8);
+    }
     p->bytes = off;
     return GF2_OK;
 }
@@ -244,7 +253,7 @@ std::string plan_text(const Plan &p)
              (long long)p.N, (long long)[&] { long long c = 1; for (int j = 0; j < p.depth; ++j) c *= 7; return c; }(),
              (long long)(p.M >> p.depth), (long long)(p.L >> p.depth), (long long)(p.N >> p.depth), p.k, p.t,
              p.bytes);
-    return buf;
+    return p.cubic ? std::string(buf) + " cubic=1" : std::string(buf);
 }
 
 // Base case over `batch` products with dense or user layouts.
@@ -323,6 +332,16 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         if (rc) return rc;
         Bsrc = Bt;
         ldBsrc = p.ldBt;
+    }
+    if (d == 0 && p.cubic) {
+        uint64_t *BT = reinterpret_cast<uint64_t *>(scratch + p.offBt);
+        GF2_CUDA_TRY(cudaMemsetAsync(BT, 0, (size_t)(64 * p.ldBt) * 8, s));
+        DMat T{BT, n, l, p.ldBt};
+        DMat X{B->data, l, n, B->stride_words};
+        int rc = transpose_launch(T, X, s);
+        if (rc) return rc;
+        return cubic_narrow_launch(A->data, A->stride_words, m, l, BT, p.ldBt, C->data, C->stride_words, n,
+                                   accumulate, s);
     }
     if (d == 0)
         return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
@@ -732,7 +751,7 @@ int gf2_describe_plan(int64_t m, int64_t l, int64_t n, const gf2_opts *opts, cha
     rc = make_plan(m, l, n, eff, &p);
     if (rc) return rc;
     std::string t = plan_text(p) + peeled;
-    if (p.base == GF2_BASE_M4RM && m > 0 && n > 0) {
+    if (p.base == GF2_BASE_M4RM && !p.cubic && m > 0 && n > 0) {
         int k = o.k, tt = o.t, bm = 0, ks = 0;
         const int d = p.depth;
         int batch = 1;

@@ -132,6 +132,10 @@ struct TcLaunch {
 };
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
 int tc_s8_launch(const TcLaunch &L, cudaStream_t s);
+// Cubic product (Section 2.3) for at most 64 columns of C: BT = the n
+// columns of B as rows, 64 rows (rows n..63 zero), stride ldbt words.
+int cubic_narrow_launch(const uint64_t *A, int64_t lda, int64_t m, int64_t l, const uint64_t *BT,
+                        int64_t ldbt, uint64_t *C, int64_t ldc, int64_t n, int accumulate, cudaStream_t s);
 
 // Autotuner cache (tune.cu): text signature -> text choice.
 bool tune_get(const std::string &key, std::string *value);

@@ -203,6 +203,42 @@ __global__ void matvec64_kernel(const uint64_t *M, int64_t rows, int64_t cols, i
     }
 }
 
+// The cubic product of Section 2.3 for a right factor of at most 64 columns
+// (the paper's choice there instead of M4RM): row i of C is one word whose
+// bit j is the parity of (row i of A) AND (row j of B^T).  One warp per row
+// of A; BT holds the n columns of B as rows (64 rows, rows n..63 zero).
+__global__ void cubic_narrow_kernel(const uint64_t *A, int64_t lda, int64_t m, int64_t l,
+                                    const uint64_t *BT, int64_t ldbt, uint64_t *C, int64_t ldc,
+                                    int64_t n, int accumulate)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t W = words_of(l);
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int vmax = (int)((n + 15) / 16) * 16;              // columns in passes of 16
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += nwarps) {
+        uint64_t y = 0;
+        for (int vb = 0; vb < vmax; vb += 16) {
+            uint64_t acc[16];
+#pragma unroll
+            for (int v = 0; v < 16; ++v) acc[v] = 0;
+            for (int64_t w = lane; w < W; w += 32) {
+                const uint64_t aw = A[i * lda + w] & word_mask(w, l);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) acc[v] ^= aw & BT[(int64_t)(vb + v) * ldbt + w];
+            }
+#pragma unroll
+            for (int v = 0; v < 16; ++v) {
+                const unsigned q = __reduce_xor_sync(0xffffffffu, (unsigned)(__popcll(acc[v]) & 1));
+                y |= (uint64_t)q << (vb + v);
+            }
+        }
+        if (lane == 0) {
+            y &= word_mask(0, n);
+            C[i * ldc] = accumulate ? (C[i * ldc] ^ y) : y;
+        }
+    }
+}
+
 __global__ void xor_count_kernel(const uint64_t *a, const uint64_t *b, int64_t n,
                                  unsigned long long *count)
 {
@@ -269,6 +305,19 @@ int matvec64_launch(const uint64_t *M, int64_t rows, int64_t cols, int64_t ld,
     if (blocks > 152 * 16) blocks = 152 * 16;
     ProfScope ps(PF_MATVEC, s);
     matvec64_kernel<<<(unsigned)blocks, 256, 0, s>>>(M, rows, cols, ld, XT, ldx, Y);
+    note_launch();
+    return check_launch();
+}
+
+int cubic_narrow_launch(const uint64_t *A, int64_t lda, int64_t m, int64_t l, const uint64_t *BT,
+                        int64_t ldbt, uint64_t *C, int64_t ldc, int64_t n, int accumulate, cudaStream_t s)
+{
+    if (m <= 0 || n <= 0) return GF2_OK;
+    if (n > 64) return GF2_EINVAL;
+    int64_t blocks = (m * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    ProfScope ps(PF_M4RM, s);
+    cubic_narrow_kernel<<<(unsigned)blocks, 256, 0, s>>>(A, lda, m, l, BT, ldbt, C, ldc, n, accumulate);
     note_launch();
     return check_launch();
 }

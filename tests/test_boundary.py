@@ -133,6 +133,17 @@ def test_plan_padding_and_scratch(lib):
     assert "depth=0" in g.gf2_describe_plan(4096, 4096, 4096)
 
 
+def test_plan_uses_the_cubic_product_for_narrow_right_factors(lib):
+    """Section 2.3: at most 64 columns of B take the cubic packed product
+    (B's columns as rows, 64 of them, in scratch)."""
+    p = g.gf2_describe_plan(5000, 3000, 40, g.opts(base=g.GF2_BASE_M4RM, depth=0))
+    assert "cubic=1" in p, p
+    assert g.gf2_scratch_bytes(5000, 3000, 40, g.opts(base=g.GF2_BASE_M4RM, depth=0)) == 64 * 48 * 8
+    assert "cubic" not in g.gf2_describe_plan(5000, 3000, 65, g.opts(base=g.GF2_BASE_M4RM, depth=0))
+    # an explicit table shape keeps the Four Russians
+    assert "cubic" not in g.gf2_describe_plan(5000, 3000, 40, g.opts(base=g.GF2_BASE_M4RM, depth=0, k=8, t=4))
+
+
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(g, "_lib", None)
     monkeypatch.setattr(g, "LIB_PATH", str(tmp_path / "absent.so"))

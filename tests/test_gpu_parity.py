@@ -120,6 +120,25 @@ def test_m4rm_tall_tiles_with_tensor_memory_half(accumulate):
         assert_same_bits(got[r0:r1], ref, n, "rows %d..%d" % (r0, r1))
 
 
+@pytest.mark.parametrize("m,l,n", [(1, 1, 1), (100, 70, 5), (5000, 3000, 63), (777, 4097, 64), (64, 129, 33)])
+@pytest.mark.parametrize("acc", [0, 1])
+def test_cubic_product_for_narrow_right_factors(m, l, n, acc):
+    A, B = inputs(m, l, n, seeds=(81, 82))
+    ref = oracle.mul_packed(A, B, m, l, n)
+    C0 = synth.random_packed(m, n, 83) if acc else None
+    if acc:
+        ref = ref ^ C0
+    o = g.opts(base=g.GF2_BASE_M4RM, depth=0, accumulate=acc)
+    assert "cubic=1" in g.gf2_describe_plan(m, l, n, o)
+    Ad, Bd = to_dev(A), to_dev(B)
+    Cd = to_dev(C0) if acc else g.empty(m, n)
+    if not acc:
+        Cd.fill_(-1)
+    g.gf2_mul(g.mat(Cd, n), g.mat(Ad, l), g.mat(Bd, n), o)
+    torch.cuda.synchronize()
+    assert_same_bits(to_host(Cd), ref, n, "cubic %s acc %d" % ((m, l, n), acc))
+
+
 def test_tail_garbage_is_ignored():
     m, l, n = 300, 200, 333
     A, B = inputs(m, l, n)
