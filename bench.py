@@ -203,6 +203,25 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
                          peaks.get("sm_max_mhz", 2070.0)}
 
 
+def strassen_stream_bytes(M, L, N, d):
+    """Algorithmic HBM bytes per product of the Strassen-Winograd additions
+    (padded sizes M, L, N, depth d): each fused two-level split reads its
+    parents and writes 49/16 of their size (7/4 for a single level), for A
+    (M x L) and B (L x N); each combine reads 49/16 (7/4) of its outputs and
+    writes them once (C-sized, M x N)."""
+    split = comb = 0.0
+    cnt, j = 1, 1
+    while j <= d:
+        step = 2 if d - j + 1 >= 2 else 1
+        f = 49.0 / 16.0 if step == 2 else 7.0 / 4.0
+        s2 = 4 ** (j - 1)
+        split += cnt * (M * L + L * N) / s2 / 8.0 * (1.0 + f)
+        comb += cnt * (M * N) / s2 / 8.0 * (1.0 + f)
+        cnt *= 49 if step == 2 else 7
+        j += step
+    return split, comb
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_0811_1714_gb300 as g
@@ -274,8 +293,18 @@ def run_ours(args, rank, world, local_rank):
         dom_ms = fam[dom]["ms"] / max(fam[dom]["launches"], 1) if fam else 0.0
         rl = roofline_for(dom, leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
             if dom in ("m4rm", "tc_fp8", "tc_s8") else None
+        hbm = {}
+        Mp, Lp, Np = (int(x) for x in kv["padded"].split("x"))
+        sb, cb = strassen_stream_bytes(Mp, Lp, Np, d)
+        for fam_name, nbytes in (("sw_split", sb), ("sw_combine", cb)):
+            if fam_name in fam and nbytes > 0:
+                per_step_ms = fam[fam_name]["ms"] / args.steps
+                gbs = nbytes / (per_step_ms * 1e-3) / 1e9
+                hbm[fam_name] = {"bound": "hbm", "bytes_per_step": nbytes, "ms_per_step": per_step_ms,
+                                 "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": gbs / peaks["hbm_gbs"]}
         results[path] = {
-            "ms": ms, "value": value, "depth": d, "plan": plan,
+            "ms": ms, "value": value, "depth": d, "plan": plan, "hbm_kernels": hbm,
             "gpu_launches": launches, "kernels": fam, "dominant": dom,
             "dominant_ms_per_launch": dom_ms, "roofline": rl,
             "freivalds_mismatched_rows": bad, "clocks": cs.summary(),
