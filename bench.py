@@ -205,20 +205,26 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
 
 def strassen_stream_bytes(M, L, N, d):
     """Algorithmic HBM bytes per product of the Strassen-Winograd additions
-    (padded sizes M, L, N, depth d): each fused two-level split reads its
-    parents and writes 49/16 of their size (7/4 for a single level), for A
-    (M x L) and B (L x N); each combine reads 49/16 (7/4) of its outputs and
-    writes them once (C-sized, M x N)."""
+    (padded sizes M, L, N, depth d), following the launch schedule: splits
+    go top-down two levels per launch (reading the parents of A, M x L, and
+    of B, L x N, writing 49 or 7 children each); combines go bottom-up two
+    levels per launch (reading 7^j products of level j, writing level j-2 or
+    j-1, C-sized at level 0)."""
     split = comb = 0.0
-    cnt, j = 1, 1
+    j = 1
     while j <= d:
         step = 2 if d - j + 1 >= 2 else 1
-        f = 49.0 / 16.0 if step == 2 else 7.0 / 4.0
-        s2 = 4 ** (j - 1)
-        split += cnt * (M * L + L * N) / s2 / 8.0 * (1.0 + f)
-        comb += cnt * (M * N) / s2 / 8.0 * (1.0 + f)
-        cnt *= 49 if step == 2 else 7
+        jt = j + step - 1
+        parents = 7 ** (j - 1)
+        children = 7 ** jt
+        split += (parents * (M * L + L * N) / 4 ** (j - 1) + children * (M * L + L * N) / 4 ** jt) / 8.0
         j += step
+    j = d
+    while j >= 1:
+        step = 2 if j >= 2 else 1
+        jp = j - step
+        comb += (7 ** j * M * N / 4 ** j + 7 ** jp * M * N / 4 ** jp) / 8.0
+        j -= step
     return split, comb
 
 
