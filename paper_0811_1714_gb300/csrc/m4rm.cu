@@ -31,7 +31,7 @@
 #include "common.cuh"
 #include "m4rm_dev.cuh"
 
-#include <mutex>
+#include <atomic>
 #include <type_traits>
 
 namespace gf2 {
@@ -69,11 +69,25 @@ __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sy
 __device__ __forceinline__ void tm_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tm_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// f(integral_constant<int, I>) for I = B .. E-1, unrolled at compile time
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
 // One CTA: a tile of BM rows x 1024 columns of C.  With TM (tall tiles),
 // the tile has two halves of NWARP*4*R rows: one in registers, the other in
 // tensor memory; the halves swap once per pass, after the first half's
 // lookups, so the tables of a pass serve twice the rows (table cost /
-// lookup cost = 2^k / BM halves) for one store + load of half a tile.
+// lookup cost = 2^k / BM halves) for one store + load of half a tile.  The
+// swap goes by chunks of 8 row-groups (one 32-column tensor-memory access):
+// a chunk is stored as soon as its lookups of the pass are done, and the
+// other half's chunk j+1 is loaded while chunk j is looked up, so that the
+// tensor-memory traffic runs behind shared-memory lookups.
 template <int KB, int NT, int R, int NWARP, bool TM>
 __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
 {
@@ -133,33 +147,18 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
         t_other = tb;
         t_free = tb + 128;
     }
-    bool have_other = false;     // the half in tensor memory has been written
     int cur = 0;                 // the half in registers
 
     uint4 acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
 
-    // registers <-> tensor memory: park the current half, fetch the other
-    auto swap_halves = [&]() {
+    // the half in tensor memory starts as zeros, so every pass can fetch it
+    if constexpr (TM) {
 #pragma unroll
-        for (int j = 0; j < R / 8; ++j)
-            tm_st32(t_free + 32 * j, *reinterpret_cast<const uint4(*)[8]>(&acc[8 * j]));
+        for (int j = 0; j < R / 8; ++j) tm_st32(t_other + 32 * j, *reinterpret_cast<const uint4(*)[8]>(&acc[8 * j]));
         tm_wait_st();
-        if (have_other) {
-#pragma unroll
-            for (int j = 0; j < R / 8; ++j) tm_ld32(t_other + 32 * j, *reinterpret_cast<uint4(*)[8]>(&acc[8 * j]));
-            tm_wait_ld();
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
-        }
-        have_other = true;
-        const uint32_t t = t_other;
-        t_other = t_free;
-        t_free = t;
-        cur ^= 1;
-    };
+    }
 
     // Stage pass g: its KG rows of B (tile columns) and the words of each
     // tile row of A that hold columns g*KG .. g*KG+KG-1.  When KG divides 128
@@ -207,8 +206,12 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
     };
 
     // ReadBits + AddRowFromTable for NT tables (Algorithms 1 and 3) on the
-    // rows of half h of the tile, pass g
-    auto lookups = [&](int g, int buf, int h) {
+    // rows of half h of the tile, pass g, row-groups J*RC .. J*RC+RC-1 (with
+    // tall tiles a chunk is the 8 row-groups one tensor-memory access moves)
+    constexpr int RC = TM ? 8 : R;
+    constexpr int NCH = R / RC;
+    auto lookups = [&](int g, int buf, int h, auto J) {
+        constexpr int rb = decltype(J)::value * RC;
         const int64_t kb = (int64_t)g * KG;
         const int64_t wa = kb >> 6;
         const int sh = (int)(kb & 63);
@@ -223,15 +226,16 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
             const uint32_t *a32 = reinterpret_cast<const uint32_t *>(arow) + 2 * aoff + (sh >> 5);
             const int s32 = sh & 31;
             const uint32_t am = (uint32_t)(mlo >> (sh & 32)) >> s32;
-            uint32_t ab[R];
+            uint32_t ab[RC];
 #pragma unroll
-            for (int r = 0; r < R; ++r) ab[r] = (a32[16 * r] >> s32) & am;
+            for (int q = 0; q < RC; ++q) ab[q] = (a32[16 * (rb + q)] >> s32) & am;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int q = 0; q < RC; ++q) {
+                const int r = rb + q;
                 uint4 a = acc[r];
 #pragma unroll
                 for (int ti = 0; ti < NT; ++ti) {
-                    const unsigned x = (ab[r] >> (ti * KB)) & IMASK;
+                    const unsigned x = (ab[q] >> (ti * KB)) & IMASK;
                     a = x4(a, tab[(ti * TROWS + (int)x) * LPR + chunk]);
                 }
                 acc[r] = a;
@@ -242,7 +246,8 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
+            for (int q = 0; q < RC; ++q) {
+                const int r = rb + q;
                 const uint2 aw = reinterpret_cast<const uint2 *>(&arow[4 * r])[aoff];
                 const uint64_t lo = ((uint64_t)aw.y << 32 | aw.x) & mlo;
                 uint64_t bits = lo >> sh;
@@ -277,10 +282,31 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
         }
         build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
         __syncthreads();                       // tables complete
-        lookups(g, buf, cur);
         if constexpr (TM) {
-            swap_halves();
-            lookups(g, buf, cur);
+            // half cur: each chunk goes to tensor memory as soon as its
+            // lookups of this pass are done, behind the next chunk's lookups
+            static_for<0, NCH>([&](auto J) {
+                lookups(g, buf, cur, J);
+                tm_st32(t_free + 32 * decltype(J)::value,
+                        *reinterpret_cast<const uint4(*)[8]>(&acc[RC * decltype(J)::value]));
+            });
+            tm_wait_st();
+            // the other half: chunk J+1 is fetched while chunk J is looked up
+            tm_ld32(t_other, *reinterpret_cast<uint4(*)[8]>(&acc[0]));
+            tm_wait_ld();
+            static_for<0, NCH>([&](auto J) {
+                constexpr int j = decltype(J)::value;
+                if constexpr (j + 1 < NCH)
+                    tm_ld32(t_other + 32 * (j + 1), *reinterpret_cast<uint4(*)[8]>(&acc[RC * (j + 1)]));
+                lookups(g, buf, cur ^ 1, J);
+                if constexpr (j + 1 < NCH) tm_wait_ld();
+            });
+            const uint32_t t = t_other;
+            t_other = t_free;
+            t_free = t;
+            cur ^= 1;
+        } else {
+            static_for<0, NCH>([&](auto J) { lookups(g, buf, cur, J); });
         }
     }
 
@@ -325,15 +351,10 @@ __global__ void __launch_bounds__(NWARP * 32, 1) m4rm_kernel(Params P)
     };
     write_half(cur);
     if constexpr (TM) {
-        // the other half: from tensor memory, or zero if no pass ran
-        if (have_other) {
+        // the other half, from tensor memory (zeros if no pass ran)
 #pragma unroll
-            for (int j = 0; j < R / 8; ++j) tm_ld32(t_other + 32 * j, *reinterpret_cast<uint4(*)[8]>(&acc[8 * j]));
-            tm_wait_ld();
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
-        }
+        for (int j = 0; j < R / 8; ++j) tm_ld32(t_other + 32 * j, *reinterpret_cast<uint4(*)[8]>(&acc[8 * j]));
+        tm_wait_ld();
         write_half(cur ^ 1);
         tm_fence_before();
         __syncthreads();
@@ -530,10 +551,16 @@ int m4rm_launch(const M4rmLaunch &L, cudaStream_t s)
     dim3 grid((unsigned)div_up(words_of(L.n), TILE_WORDS), (unsigned)div_up(L.m, v->bm),
               (unsigned)(L.batch * ks));
     if (grid.y > 65535u || grid.z > 65535u) return GF2_EUNSUPPORTED;
-    static std::mutex mu;
-    {
-        std::lock_guard<std::mutex> lk(mu);
+    // the dynamic shared-memory limit is set once per variant and device
+    // (bit d of the variant's mask; devices past 63 set it on every launch)
+    static std::atomic<uint64_t> attr_set[sizeof(kVariants) / sizeof(kVariants[0])];
+    int dev = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    std::atomic<uint64_t> &done = attr_set[v - kVariants];
+    const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (!bit || !(done.load(std::memory_order_acquire) & bit)) {
         GF2_CUDA_TRY(cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v->smem));
+        done.fetch_or(bit, std::memory_order_acq_rel);
     }
     ProfScope ps(PF_M4RM, s);
     v->fn<<<grid, v->nw * 32, v->smem, s>>>(P);
