@@ -324,11 +324,15 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         }
     }
     if (b_ready) GF2_CUDA_TRY(cudaStreamWaitEvent(s, b_ready, 0));
+    // the FP8 base case reads B^T with each 32-bit half bit-reversed (its
+    // expansion order); the transpose writes it so, with the tail beyond l
+    // already cleared
+    const bool rev32 = (p.base == GF2_BASE_TC_FP8);
     if (tc) {
         uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
         DMat T{Bt, n, l, p.ldBt};
         DMat X{B->data, l, n, B->stride_words};
-        int rc = transpose_launch(T, X, s);
+        int rc = transpose_launch(T, X, s, rev32);
         if (rc) return rc;
         Bsrc = Bt;
         ldBsrc = p.ldBt;
@@ -363,7 +367,11 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
             // (B_SW)^T and SW is (B_NE)^T; side 2 swaps their roles
             SB.side = 2; SB.rows = Np; SB.cols = Lp;
             if (j == 1) {
-                SB.X = Bsrc; SB.ld = ldBsrc; SB.bs = 0; SB.vrows = n; SB.vcols = l;
+                // the tail beyond l is zero already; with reversed halves a
+                // mask at column l would cut the wrong bits, so the split
+                // takes whole words
+                SB.X = Bsrc; SB.ld = ldBsrc; SB.bs = 0; SB.vrows = n;
+                SB.vcols = rev32 ? words_of(l) * 64 : l;
             } else {
                 SB.X = reinterpret_cast<const uint64_t *>(scratch + p.offB[j - 1]);
                 SB.ld = p.ldB[j - 1]; SB.bs = p.slabB[j - 1]; SB.vrows = Np; SB.vcols = Lp;

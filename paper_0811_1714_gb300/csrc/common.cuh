@@ -111,7 +111,8 @@ int sw_combine2_launch(const CombineLaunch &L, cudaStream_t s);
 
 // Utilities.
 int random_launch(DMat M, uint64_t seed, double p, cudaStream_t s);
-int transpose_launch(DMat T, DMat X, cudaStream_t s);
+// T = X^T; rev32: the bits of each 32-bit half of T's words reversed
+int transpose_launch(DMat T, DMat X, cudaStream_t s, bool rev32 = false);
 int zero_launch(DMat M, cudaStream_t s);   // clears rows x stride words
 // Y (rows words) = M X with X one word per column of M (64 vectors).
 int matvec64_launch(const uint64_t *M, int64_t rows, int64_t cols, int64_t ld,

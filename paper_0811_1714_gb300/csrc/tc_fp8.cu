@@ -14,8 +14,12 @@
 // the last mantissa bit of D + 256 (whose ulp is 2^-15); parities of
 // successive chunks are XORed, which is the GF(2) sum over the whole K range.
 // The position-dependent values let a byte of bits expand with one byte
-// permute and one mask per 4 entries (B's bits are first reversed, so the
-// mask picks them in the opposite order).
+// permute and one mask per 4 entries.  B's values run the other way, so its
+// bits are taken reversed: the transpose that produces B^T stores each
+// 32-bit half of a word bit-reversed, and no reversal is left for the
+// unpackers.  Only A's K tail is masked (in the last K block): an entry of A
+// beyond K is 0, and every B byte is a finite FP8 value, so B's entries
+// there add nothing whatever they hold.
 //
 // Layout of one CTA (persistent, one per SM, 26 warps):
 //   warps 0-3   epilogue: tcgen05.ld of the 128 x 192 FP32 accumulator (warp
@@ -300,9 +304,10 @@ __device__ __forceinline__ void expand_a(uint32_t x, uint32_t *out)
     }
 }
 
-// B: as expand_a with bit 4n+i moved to bit 3-i (value 2^(-6-i)).  In the
-// bit-reversed word r, nibble n of x is nibble 7-n with its bits reversed,
-// so replicating its byte and masking bit 3-i of copy i does it.
+// B: as expand_a with bit 4n+i moved to bit 3-i (value 2^(-6-i)).  B^T's
+// 32-bit halves arrive bit-reversed (r): nibble n of the natural half x is
+// nibble 7-n of r with its bits reversed, so replicating its byte and
+// masking bit 3-i of copy i does it.
 __device__ __forceinline__ uint32_t expand_b_nibble(uint32_t r, uint32_t rs, int n)
 {
     const int m = 7 - n;                       // nibble of r
@@ -447,9 +452,12 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             if (!warp_wait(empty_bar(s), (uint32_t)((q / STAGES) & 1) ^ 1u, P.status, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const uint64_t *pk = reinterpret_cast<const uint64_t *>(pbase + ps * PSTAGE_BYTES) + KW * row;
-            // words beyond K arrive as zeros; bits beyond K in the last word are masked
-            const uint64_t w0 = pk[2 * h] & word_mask(kb * KW + 2 * h, T.l);
-            const uint64_t w1 = pk[2 * h + 1] & word_mask(kb * KW + 2 * h + 1, T.l);
+            // A's entries beyond K (only in the last K block) are masked to 0
+            uint64_t w0 = pk[2 * h], w1 = pk[2 * h + 1];
+            if (kb == T.nkb - 1) {
+                w0 &= word_mask(kb * KW + 2 * h, T.l);
+                w1 &= word_mask(kb * KW + 2 * h + 1, T.l);
+            }
             uint32_t v[32];                            // K entries 128h + 4j .. 4j+3 in v[j]
             expand_a((uint32_t)w0, v);
             expand_a((uint32_t)(w0 >> 32), v + 8);
@@ -487,10 +495,10 @@ tc_fp8_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             unsigned char *st = sbase + s * STAGE_BYTES + rowoff;
 #pragma unroll
             for (int sub = 0; sub < 2; ++sub) {
-                const uint64_t wv = pk[2 * sub + half] & word_mask(kb * KW + 2 * sub + half, T.l);
+                const uint64_t wv = pk[2 * sub + half];       // halves bit-reversed, tail unmasked
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
-                    const uint32_t r = __brev((uint32_t)(wv >> (32 * hh)));
+                    const uint32_t r = (uint32_t)(wv >> (32 * hh));
                     const uint32_t rs = r >> 4;
 #pragma unroll
                     for (int q2 = 0; q2 < 2; ++q2) {        // 16 entries -> one 16-byte chunk
@@ -680,7 +688,9 @@ int make_map(CUtensorMap *map, const uint64_t *base, int64_t words, int64_t rows
 // ------------------------------------------------------------------ batched form
 // B^T of every product of a batch in one launch: one warp per 64 x 64 block
 // (a ballot over the lanes of bit j gathers column j); the block's product
-// is found by binary search over the prefix sums of the block counts.
+// is found by binary search over the prefix sums of the block counts.  Each
+// 32-bit half of an output word is stored bit-reversed, the order the
+// unpackers expand.
 struct TDesc {
     const uint64_t *X;
     uint64_t *T;
@@ -719,9 +729,13 @@ __global__ void transpose_batched_kernel(const TDesc *__restrict__ d, const long
             }
         }
         const uint64_t tm = word_mask(rb, D.rows);
+        out0 &= tm;
+        out1 &= tm;
+        out0 = ((uint64_t)__brev((uint32_t)(out0 >> 32)) << 32) | __brev((uint32_t)out0);
+        out1 = ((uint64_t)__brev((uint32_t)(out1 >> 32)) << 32) | __brev((uint32_t)out1);
         const int64_t t0 = cb * 64 + lane, t1 = t0 + 32;
-        if (t0 < D.cols) D.T[t0 * D.ldt + rb] = out0 & tm;
-        if (t1 < D.cols) D.T[t1 * D.ldt + rb] = out1 & tm;
+        if (t0 < D.cols) D.T[t0 * D.ldt + rb] = out0;
+        if (t1 < D.cols) D.T[t1 * D.ldt + rb] = out1;
     }
 }
 

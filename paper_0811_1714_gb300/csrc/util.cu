@@ -137,8 +137,10 @@ __global__ void seeded_words_kernel(uint64_t *X, int64_t n, uint64_t seed)
 }
 
 // T = X^T, one warp per 64 x 64 block: lane i holds rows i and i+32 of the
-// block; a ballot over the lanes of bit j gathers column j.
-__global__ void transpose_kernel(DMat T, DMat X)
+// block; a ballot over the lanes of bit j gathers column j.  With rev32 the
+// bits of each 32-bit half of every output word are stored reversed (bit b
+// of the half at 31 - b), the order the FP8 tensor-core base case expands.
+__global__ void transpose_kernel(DMat T, DMat X, int rev32)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -166,9 +168,15 @@ __global__ void transpose_kernel(DMat T, DMat X)
         }
         // out0: row cb*64+lane of T, word rb; out1: row cb*64+32+lane
         const uint64_t tm = word_mask(rb, T.cols);
+        out0 &= tm;
+        out1 &= tm;
+        if (rev32) {
+            out0 = ((uint64_t)__brev((uint32_t)(out0 >> 32)) << 32) | __brev((uint32_t)out0);
+            out1 = ((uint64_t)__brev((uint32_t)(out1 >> 32)) << 32) | __brev((uint32_t)out1);
+        }
         const int64_t t0 = cb * 64 + lane, t1 = t0 + 32;
-        if (t0 < T.rows) T.p[t0 * T.ld + rb] = out0 & tm;
-        if (t1 < T.rows) T.p[t1 * T.ld + rb] = out1 & tm;
+        if (t0 < T.rows) T.p[t0 * T.ld + rb] = out0;
+        if (t1 < T.rows) T.p[t1 * T.ld + rb] = out1;
     }
 }
 
@@ -283,14 +291,14 @@ int seeded_words_launch(uint64_t *X, int64_t n, uint64_t seed, cudaStream_t s)
     return check_launch();
 }
 
-int transpose_launch(DMat T, DMat X, cudaStream_t s)
+int transpose_launch(DMat T, DMat X, cudaStream_t s, bool rev32)
 {
     const int64_t nblk = ((X.rows + 63) / 64) * words_of(X.cols);
     if (nblk <= 0) return GF2_OK;
     int64_t blocks = (nblk * 32 + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
     ProfScope ps(PF_TRANSPOSE, s);
-    transpose_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, X);
+    transpose_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, X, rev32 ? 1 : 0);
     note_launch();
     return check_launch();
 }
