@@ -34,9 +34,9 @@ METRIC = "effective GF(2) bit-ops/s (2mnk/t) at n=32768, bit-exact"
 # profiles/m4rm_kernel_n16384_depth2.md): bytes read + written per byte of leaf
 # operands (A, B, C slabs), valid while the kernel sources hash to "sha".
 NCU_TRAFFIC = {
-    "m4rm": {"sha": "4b5e18cf1cd68133", "sources": ["paper_0811_1714_gb300/csrc/m4rm.cu",
+    "m4rm": {"sha": "459f362071b4ddff", "sources": ["paper_0811_1714_gb300/csrc/m4rm.cu",
                                          "paper_0811_1714_gb300/csrc/m4rm_dev.cuh"],
-             "bytes_per_operand_byte": 0.8752},
+             "bytes_per_operand_byte": 0.8845},
 }
 
 
@@ -80,9 +80,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of one CPU-oracle sample")
-    ap.add_argument("--workload", choices=["square", "batched", "chain"], default="square",
+    ap.add_argument("--workload", choices=["square", "batched", "chain", "sweep"], default="square",
                     help="square: the n x n product (default); batched: 4096 products, "
-                         "dimensions log-uniform in [64, 2048], one persistent launch")
+                         "dimensions log-uniform in [64, 2048], one persistent launch; "
+                         "sweep: packed M4RM over Strassen depth x k at n = 8192, 16384, "
+                         "32768 and 20000x12000.12000x28000")
     return ap.parse_args()
 
 
@@ -561,6 +563,57 @@ def run_chain(args, rank, world, local_rank):
     }
 
 
+def run_sweep(args, rank, world, local_rank):
+    """Packed M4RM over Strassen-Winograd depth (the cutoff) x k (bits per
+    table; t automatic) on the square 8192, 16384 and 32768 products and on
+    20000x12000 . 12000x28000.  Every point is timed by CUDA events (one
+    warm-up, `steps` timed calls) and Freivalds-checked."""
+    import torch
+    import paper_0811_1714_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    shapes = [(8192, 8192, 8192), (16384, 16384, 16384), (32768, 32768, 32768), (20000, 12000, 28000)]
+    ks = [4, 5, 6, 7, 8, 9, 10]
+    points, failed = [], 0
+    for (m, l, n) in shapes:
+        A, B, C = g.empty(m, l), g.empty(l, n), g.empty(m, n)
+        MA, MB, MC = g.mat(A, l), g.mat(B, n), g.mat(C, n)
+        g.gf2_random(MA, 1 + 100 * rank)
+        g.gf2_random(MB, 2 + 100 * rank)
+        depth = 0
+        while min(m, l, n) >> depth >= 1024:
+            for k in ks:
+                o = g.opts(base=g.GF2_BASE_M4RM, depth=depth, k=k, peel=0)
+                g.gf2_mul(MC, MA, MB, o)
+                torch.cuda.synchronize()
+                ev[0].record(stream)
+                for _ in range(max(1, args.steps)):
+                    g.gf2_mul(MC, MA, MB, o)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                ms = ev[0].elapsed_time(ev[1]) / max(1, args.steps)
+                ok = g.gf2_freivalds(MC, MA, MB, 4242) == 0
+                failed += 0 if ok else 1
+                points.append({"m": m, "l": l, "n": n, "depth": depth, "k": k, "ms": ms,
+                               "bit_ops_per_s": 2.0 * m * l * n / (ms * 1e-3), "freivalds_ok": ok,
+                               "plan": g.gf2_describe_plan(m, l, n, o)})
+            depth += 1
+        del A, B, C
+        torch.cuda.empty_cache()
+    best = max((p for p in points if p["n"] == 32768 and p["m"] == 32768), key=lambda p: p["bit_ops_per_s"])
+    return {
+        "metric": "effective GF(2) bit-ops/s (2mnk/t), packed M4RM over depth x k", "value": best["bit_ops_per_s"],
+        "unit": "bit-ops/s", "n_gpus": world, "steps": args.steps, "warmup": 1,
+        "ms_per_step": best["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64-packed-bits", "data": "synthetic: SplitMix64 Bernoulli(1/2) bits, seeds 1/2",
+        "config": {"workload": "sweep of Strassen-Winograd depth x M4RM k", "best_at_32768": best},
+        "sweep": points, "verified": {"freivalds_failures": failed},
+    }
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -575,8 +628,9 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload in ("batched", "chain"):
-        line = (run_batched if args.workload == "batched" else run_chain)(args, rank, world, local_rank)
+    if args.workload in ("batched", "chain", "sweep"):
+        run = {"batched": run_batched, "chain": run_chain, "sweep": run_sweep}[args.workload]
+        line = run(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

@@ -474,20 +474,24 @@ void m4rm_pick(int64_t m, int64_t l, int64_t n, int batch, int *k, int *t, int *
     // Shared-memory wavefronts per bit of K of one tile (table-row reads,
     // table build, A-index and staged-B reads), counted for the default
     // (k, t) of each height: 2048 rows k=8 t=4, 1024 rows k=8 t=4, 256 rows
-    // k=6 t=8, 64 rows k=4 t=8.  Among the heights that give every SM two
-    // CTAs, take the one that minimises tiles x cost: a ragged m (2111
-    // rows, say) is cheaper in 256-row tiles than in two 2048-row tiles.
+    // k=6 t=8, 64 rows k=4 t=8; and the CTAs of that variant one SM holds
+    // (they share its shared-memory bandwidth).  The estimate is waves x
+    // resident CTAs x cost: with many tiles it is tiles x cost / SMs (a
+    // ragged m, 2111 rows say, is cheaper in 256-row tiles than in two
+    // 2048-row ones), and with few it charges the partly empty last wave.
+    // A shorter tile has to win by 5 %: the costs are estimates.
     const int bms[4] = {2048, 1024, 256, 64};
     const double cost[4] = {316.0, 180.0, 56.8, 22.5};
+    const int occ[4] = {1, 1, 2, 4};
     int b = 64;
     double best = 1e300;
     for (int i = 0; i < 4; ++i) {
         if (bms[i] == 2048 && m <= 1024) continue;  // the tensor-memory half would hold no rows
         const int64_t tm = (m + bms[i] - 1) / bms[i];
         const int64_t ctas = (int64_t)batch * tn * tm;
-        if (ctas < 2 * sms) continue;
-        const double c = (double)tm * cost[i];
-        if (c < best) { best = c; b = bms[i]; }
+        const int64_t slots = (int64_t)sms * occ[i];
+        const double c = (double)((ctas + slots - 1) / slots) * occ[i] * cost[i];
+        if (c < 0.95 * best) { best = c; b = bms[i]; }
     }
     int kk = (b >= 1024) ? 8 : (b == 256 ? 6 : 4);
     int tt = (b >= 1024) ? 4 : 8;
@@ -504,8 +508,10 @@ void m4rm_pick(int64_t m, int64_t l, int64_t n, int batch, int *k, int *t, int *
     }
     const int64_t ctas = (int64_t)batch * tn * ((m + b - 1) / b);
     const int64_t groups = (l + kk * tt - 1) / (kk * tt);
+    // split K (partial products XORed into C) only when two or more splits
+    // of every tile fit in one wave
     int ks = 1;
-    if (ctas < sms && groups > 1) {
+    if (2 * ctas <= sms && groups > 1) {
         ks = (int)((sms + ctas - 1) / ctas);
         if (ks > groups) ks = (int)groups;
         if (ks > 64) ks = 64;
