@@ -597,8 +597,9 @@ int choose_peel(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts &
     oq.peel = 1;
     int rc = gf2_mul(C, A, B, &op, stream);              // warms (and tunes) the padded plan
     if (rc) return rc;
-    cudaEvent_t e[3];
-    for (auto &ev : e) GF2_CUDA_TRY(cudaEventCreate(&ev));
+    ScopedEvents<3> ev;
+    if ((rc = ev.create())) return rc;
+    cudaEvent_t *e = ev.e;
     float t_pad = 0.f, t_peel = 0.f;
     cudaEventRecord(e[0], s);
     rc = gf2_mul(C, A, B, &op, stream);
@@ -609,7 +610,6 @@ int choose_peel(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts &
         cudaEventElapsedTime(&t_pad, e[0], e[1]);
         cudaEventElapsedTime(&t_peel, e[1], e[2]);
     }
-    for (auto &ev : e) cudaEventDestroy(ev);
     if (rc) return rc;
     tune_put(key, t_peel < t_pad ? "peel" : "pad");
     return 2;
@@ -940,9 +940,9 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
         if (rc) return rc;
     } else {
         // time every candidate on these operands (each computes the same C)
-        cudaEvent_t e0, e1;
-        GF2_CUDA_TRY(cudaEventCreate(&e0));
-        GF2_CUDA_TRY(cudaEventCreate(&e1));
+        ScopedEvents<2> ev;
+        if ((rc = ev.create())) return rc;
+        cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
         size_t best = 0;
         float best_ms = 1e30f;
         if (b_ready) GF2_CUDA_TRY(cudaStreamWaitEvent(s, b_ready, 0));
@@ -956,8 +956,6 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
             if (rc == GF2_OK && ms < best_ms) { best_ms = ms; best = i; }
             if (rc) break;
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         if (rc) return rc;
         if (best + 1 != plans.size()) {     // leave the chosen plan's result, as a plain call would
             rc = mul_device(&dC, &dA, &dB, plans[best], 0, base, s);

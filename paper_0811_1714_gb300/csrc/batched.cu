@@ -539,15 +539,16 @@ int launch_variant(const BVariant &v, const BProd *dp, const void *dt, int ntile
 }
 
 // Times every candidate on this batch (two runs each after one warm-up) and
-// returns the index of the fastest.
+// returns the index of the fastest, or GF2_ECUDA when its timing events
+// cannot be created.
 int autotune(const std::vector<BProd> &prods, int accumulate, cudaStream_t s)
 {
     const auto &vs = bvariants();
     int best = 0;
     float best_ms = 1e30f;
-    cudaEvent_t e0, e1;
-    GF2_CUDA_TRY(cudaEventCreate(&e0));
-    GF2_CUDA_TRY(cudaEventCreate(&e1));
+    ScopedEvents<2> ev;
+    if (ev.create()) return GF2_ECUDA;
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     for (size_t i = 0; i < vs.size(); ++i) {
         std::vector<unsigned char> tiles;
         int nt = 0;
@@ -575,8 +576,6 @@ int autotune(const std::vector<BProd> &prods, int accumulate, cudaStream_t s)
             best = (int)i;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return best;
 }
 
@@ -643,6 +642,7 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
                 if (name == vs[i].name) vi = (int)i;
         if (vi < 0) {
             vi = autotune(prods, accumulate, s);
+            if (vi < 0) return vi;                    // a CUDA error while timing
             tune_put(sig, vs[vi].name);
         }
     }

@@ -165,3 +165,31 @@ bool tc_fp8_available();
         cudaError_t e_ = (expr);                               \
         if (e_ != cudaSuccess) return GF2_ECUDA;               \
     } while (0)
+
+namespace gf2 {
+
+// Timing events owned for the length of a scope: every one that was created
+// is destroyed on every return path.
+template <int N>
+struct ScopedEvents {
+    cudaEvent_t e[N] = {};
+    ScopedEvents() = default;
+    ScopedEvents(const ScopedEvents &) = delete;
+    ScopedEvents &operator=(const ScopedEvents &) = delete;
+    ~ScopedEvents()
+    {
+        for (cudaEvent_t ev : e)
+            if (ev) cudaEventDestroy(ev);
+    }
+    int create()
+    {
+        for (cudaEvent_t &ev : e)
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                ev = nullptr;
+                return GF2_ECUDA;
+            }
+        return GF2_OK;
+    }
+};
+
+}  // namespace gf2

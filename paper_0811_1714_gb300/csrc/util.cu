@@ -45,6 +45,8 @@ ProfScope::ProfScope(int family, cudaStream_t stream) : fam(family), s(stream), 
     if (cudaEventCreate(&r->a) != cudaSuccess || cudaEventCreate(&r->b) != cudaSuccess ||
         cudaEventRecord(r->a, stream) != cudaSuccess) {
         cudaGetLastError();
+        if (r->a) cudaEventDestroy(r->a);
+        if (r->b) cudaEventDestroy(r->b);
         delete r;
         return;
     }
