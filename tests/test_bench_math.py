@@ -1,0 +1,50 @@
+"""The bench's algorithmic byte counts, checked on the CPU against closed forms.
+
+The Strassen-Winograd additions (Algorithm 4) write 7 operands of a quarter
+of the parent's size per level and per side.  The library fuses two levels
+per launch where it can: splits top-down (levels 1-2, then 3-4, ...; a single
+last level when the depth is odd), combines bottom-up (levels d..d-1, ...; a
+single level 1 when the depth is odd).  The expected totals below are those
+schedules written out by hand in units of a whole operand, (M L + L N) / 8
+bytes for the splits and M N / 8 for the combines.
+"""
+import pytest
+
+import bench
+
+M = L = N = 32768
+SPLIT_UNIT = (M * L + L * N) / 8.0
+COMB_UNIT = M * N / 8.0
+
+# depth: (split traffic, combine traffic) in units of one operand
+CLOSED = {
+    0: (0.0, 0.0),
+    1: (1 + 7 / 4, 7 / 4 + 1),
+    2: (1 + 49 / 16, 49 / 16 + 1),
+    3: ((1 + 49 / 16) + (49 / 16 + 343 / 64), (343 / 64 + 7 / 4) + (7 / 4 + 1)),
+    4: ((1 + 49 / 16) + (49 / 16 + 2401 / 256), (2401 / 256 + 49 / 16) + (49 / 16 + 1)),
+    5: ((1 + 49 / 16) + (49 / 16 + 2401 / 256) + (2401 / 256 + 16807 / 1024),
+        (16807 / 1024 + 343 / 64) + (343 / 64 + 7 / 4) + (7 / 4 + 1)),
+}
+
+
+@pytest.mark.parametrize("depth", sorted(CLOSED))
+def test_strassen_stream_bytes_closed_forms(depth):
+    split, comb = bench.strassen_stream_bytes(M, L, N, depth)
+    es, ec = CLOSED[depth]
+    assert split == pytest.approx(es * SPLIT_UNIT, rel=1e-12)
+    assert comb == pytest.approx(ec * COMB_UNIT, rel=1e-12)
+
+
+def test_depth4_totals_at_n32768():
+    """4.43 GB of split traffic and 2.22 GB of combine traffic per product."""
+    split, comb = bench.strassen_stream_bytes(M, L, N, 4)
+    assert round(split / 1e9, 2) == 4.43
+    assert round(comb / 1e9, 2) == 2.22
+
+
+def test_rectangular_shapes_scale_per_side():
+    """A side's traffic scales with that side's operand only."""
+    s1, c1 = bench.strassen_stream_bytes(4096, 8192, 2048, 2)
+    assert s1 == pytest.approx((1 + 49 / 16) * (4096 * 8192 + 8192 * 2048) / 8.0)
+    assert c1 == pytest.approx((49 / 16 + 1) * 4096 * 2048 / 8.0)
