@@ -48,3 +48,28 @@ def test_rectangular_shapes_scale_per_side():
     s1, c1 = bench.strassen_stream_bytes(4096, 8192, 2048, 2)
     assert s1 == pytest.approx((1 + 49 / 16) * (4096 * 8192 + 8192 * 2048) / 8.0)
     assert c1 == pytest.approx((49 / 16 + 1) * 4096 * 2048 / 8.0)
+
+
+PEAKS = {"hbm_gbs": 6780.7, "bf16_tflops": 1896.1, "sm_max_mhz": 2070.0}
+
+
+def test_m4rm_roofline_counts_table_row_reads():
+    """n = 32768 at depth 4: 2401 leaves of 2048^3, k = 8, so one launch
+    reads 2401 * 2048^3 / 64 = 3.22e11 table bytes; at 11.47 ms that is
+    28.1 TB/s of a 152 x 128 B x 2070 MHz = 40.27 TB/s shared-memory peak."""
+    r = bench.roofline_for("m4rm", 2401, 2048, 2048, 2048, 8, 11.47, PEAKS, "measured")
+    assert r["bound"] == "smem" and r["unit"] == "GB/s"
+    assert 2401 * 2048 ** 3 / 64 == pytest.approx(3.2226e11, rel=1e-4)
+    assert r["peak"] == pytest.approx(40273.92)
+    assert r["achieved"] == pytest.approx(3.2226e11 / 11.47e-3 / 1e9, rel=1e-4)
+    assert round(r["frac"], 3) == 0.698
+
+
+def test_tc_roofline_counts_dense_flops_against_twice_bf16():
+    """n = 32768 at depth 3: 343 leaves of 4096^3, 2 M L N flops each, against
+    2 x the measured bf16 rate (the nominal FP8 / BF16 ratio)."""
+    r = bench.roofline_for("tc_fp8", 343, 4096, 4096, 4096, 0, 21.5, PEAKS, "measured")
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["peak"] == pytest.approx(3792.2)
+    assert r["achieved"] == pytest.approx(2.0 * 4096 ** 3 * 343 / 21.5e-3 / 1e12)
+    assert round(r["frac"], 2) == 0.58
