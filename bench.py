@@ -43,6 +43,9 @@ NCU_TRAFFIC = {
 # int8 warp-level tensor rate (mma.sync m16n8k32 .s8, dense) measured on a GB300
 # with register-resident operands: the peak for the int8 base case.
 S8_MMA_SYNC_TOPS = 150.3
+# binary warp-level tensor rate (mma.sync m16n8k256 .b1 .and.popc: AND + popcount
+# per bit pair), measured the same way: the peak for the binary base case.
+B1_MMA_SYNC_TOPS = 146.2
 
 
 def ncu_traffic(fam, leaves, M, L, N):
@@ -72,7 +75,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--p", type=float, default=0.5, help="density of one bits (square workload)")
-    ap.add_argument("--paths", default="m4rm,tc_fp8,tc_s8", help="base cases to time")
+    ap.add_argument("--paths", default="m4rm,tc_fp8,tc_s8,tc_b1", help="base cases to time")
     ap.add_argument("--depth", type=int, default=-1)
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--t", type=int, default=0)
@@ -186,6 +189,13 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_note": "2 x bf16 burst of %s peaks (nominal fp8/bf16 ratio)" % peak_kind}
+    if fam == "tc_b1":
+        ops = 2.0 * M * L * N * leaves                      # AND + popcount per bit pair, int32 sums
+        achieved = ops / (ms_per_launch * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": B1_MMA_SYNC_TOPS, "unit": "TOPS",
+                "frac": achieved / B1_MMA_SYNC_TOPS, "traffic": None,
+                "peak_note": "mma.sync m16n8k256 b1 and.popc rate measured on this GPU by a "
+                             "register-only throughput loop (tcgen05 has no binary kind on sm_103a)"}
     if fam == "tc_s8":
         ops = 2.0 * M * L * N * leaves                      # dense 0/1 int8 product, int32 sums
         achieved = ops / (ms_per_launch * 1e-3) / 1e12
@@ -253,7 +263,8 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_kind = load_peaks()
 
     avail = [p.strip() for p in args.paths.split(",") if p.strip()]
-    base_of = {"m4rm": g.GF2_BASE_M4RM, "tc_fp8": g.GF2_BASE_TC_FP8, "tc_s8": g.GF2_BASE_TC_S8}
+    base_of = {"m4rm": g.GF2_BASE_M4RM, "tc_fp8": g.GF2_BASE_TC_FP8, "tc_s8": g.GF2_BASE_TC_S8,
+               "tc_b1": g.GF2_BASE_TC_B1}
     results = {}
     for path in avail:
         o = g.opts(base=base_of[path], depth=args.depth, k=args.k if path == "m4rm" else 0,
@@ -300,7 +311,7 @@ def run_ours(args, rank, world, local_rank):
         dom = max(fam.items(), key=lambda kvp: kvp[1]["ms"])[0] if fam else path
         dom_ms = fam[dom]["ms"] / max(fam[dom]["launches"], 1) if fam else 0.0
         rl = roofline_for(dom, leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
-            if dom in ("m4rm", "tc_fp8", "tc_s8") else None
+            if dom in ("m4rm", "tc_fp8", "tc_s8", "tc_b1") else None
         hbm = {}
         Mp, Lp, Np = (int(x) for x in kv["padded"].split("x"))
         sb, cb = strassen_stream_bytes(Mp, Lp, Np, d)

@@ -65,6 +65,10 @@ extern "C" {
 #define GF2_BASE_TC_FP8 2      /* 0/1 FP8 e4m3 tensor-core product, parity of exact sums    */
 #define GF2_BASE_TC_S8  3      /* 0/1 int8 warp-level tensor product (mma.sync), int32 sums;
                                   never chosen automatically (slow on this part)             */
+#define GF2_BASE_TC_B1  4      /* binary warp-level tensor product on the packed words
+                                  (mma.sync .b1 .and.popc, Section 2.3's popcount of
+                                  AND-ed rows of A and B^T), int32 sums; never chosen
+                                  automatically (slow on this part)                          */
 
 typedef struct gf2_mat {
     uint64_t *data;        /* first word of row 0                                  */
@@ -252,7 +256,8 @@ int gf2_selftest_wait(int64_t limit_cycles, void *cuda_stream);
  * device time (ms) and launch count of one kernel family:
  *   0 m4rm base case, 1 tensor-core base case, 2 Strassen split,
  *   3 Strassen combine, 4 transpose, 5 generator, 6 Freivalds products,
- *   7 MakeTable, 8 batched base case, 9 int8 tensor-core base case.
+ *   7 MakeTable, 8 batched base case, 9 int8 tensor-core base case,
+ *   10 binary tensor-core base case.
  * gf2_profile_name gives the family's name (NULL beyond the last one).
  */
 int gf2_profile_enable(int32_t on);

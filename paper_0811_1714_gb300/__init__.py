@@ -45,6 +45,7 @@ GF2_BASE_AUTO = 0
 GF2_BASE_M4RM = 1
 GF2_BASE_TC_FP8 = 2
 GF2_BASE_TC_S8 = 3
+GF2_BASE_TC_B1 = 4
 
 #: every symbol declared in include/gf2.h
 EXPORTS = (
@@ -370,7 +371,7 @@ def gf2_profile_name(family: int):
 
 
 PROFILE_FAMILIES = ("m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose", "random",
-                    "freivalds", "make_table", "batched", "tc_s8")
+                    "freivalds", "make_table", "batched", "tc_s8", "tc_b1")
 
 
 # ---- torch conveniences ----------------------------------------------------

@@ -24,6 +24,22 @@ using namespace gf2;
 
 namespace {
 
+// The tensor-core base cases read B transposed (rows of B^T = columns of B).
+bool is_tc(int base)
+{
+    return base == GF2_BASE_TC_FP8 || base == GF2_BASE_TC_S8 || base == GF2_BASE_TC_B1;
+}
+
+const char *base_name(int base)
+{
+    switch (base) {
+    case GF2_BASE_TC_FP8: return "tc_fp8";
+    case GF2_BASE_TC_S8: return "tc_s8";
+    case GF2_BASE_TC_B1: return "tc_b1";
+    default: return "m4rm";
+    }
+}
+
 // ---------------------------------------------------------------- arenas
 // One arena per (device, stream).  A caller holds the arena's mutex from
 // arena_get until it has queued all work that uses the arena, so another
@@ -134,7 +150,7 @@ gf2_opts resolve(const gf2_opts *o)
 
 int check_opts(const gf2_opts &o)
 {
-    if (o.base < GF2_BASE_AUTO || o.base > GF2_BASE_TC_S8) return GF2_EINVAL;
+    if (o.base < GF2_BASE_AUTO || o.base > GF2_BASE_TC_B1) return GF2_EINVAL;
     if (o.depth < -1 || o.depth > 8) return GF2_EINVAL;
     if (o.k < 0 || o.k > 10 || o.t < 0 || o.t > 16) return GF2_EINVAL;
     if (o.accumulate != 0 && o.accumulate != 1) return GF2_EINVAL;
@@ -202,7 +218,7 @@ int make_plan(int64_t m, int64_t l, int64_t n, const gf2_opts &o, Plan *p)
     p->N = d ? round_up(n, cq) : n;
     if (d && (p->M < 2 * rq / 2 || p->M / rq < 1)) return GF2_EUNSUPPORTED;
     p->k = o.k; p->t = o.t;
-    const bool tc = (p->base == GF2_BASE_TC_FP8 || p->base == GF2_BASE_TC_S8);   // B held transposed
+    const bool tc = is_tc(p->base);   // B held transposed
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t at = off;
@@ -249,7 +265,7 @@ std::string plan_text(const Plan &p)
     char buf[512];
     snprintf(buf, sizeof buf,
              "base=%s depth=%d padded=%lldx%lldx%lld leaves=%lld leaf=%lldx%lldx%lld k=%d t=%d scratch=%zu",
-             p.base == GF2_BASE_TC_FP8 ? "tc_fp8" : (p.base == GF2_BASE_TC_S8 ? "tc_s8" : "m4rm"), p.depth, (long long)p.M, (long long)p.L,
+             base_name(p.base), p.depth, (long long)p.M, (long long)p.L,
              (long long)p.N, (long long)[&] { long long c = 1; for (int j = 0; j < p.depth; ++j) c *= 7; return c; }(),
              (long long)(p.M >> p.depth), (long long)(p.L >> p.depth), (long long)(p.N >> p.depth), p.k, p.t,
              p.bytes);
@@ -261,14 +277,15 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
              int64_t ldb, int64_t bsB, uint64_t *C, int64_t ldc, int64_t bsC, int64_t m, int64_t l,
              int64_t n, int batch, int accumulate, cudaStream_t s)
 {
-    if (p.base == GF2_BASE_TC_FP8 || p.base == GF2_BASE_TC_S8) {
+    if (is_tc(p.base)) {
         TcLaunch L;
         L.A = A; L.lda = lda; L.bsA = bsA;
         L.Bt = B; L.ldb = ldb; L.bsB = bsB;
         L.C = C; L.ldc = ldc; L.bsC = bsC;
         L.m = m; L.l = l; L.n = n; L.batch = batch; L.accumulate = accumulate;
         L.status = nullptr;
-        return p.base == GF2_BASE_TC_S8 ? tc_s8_launch(L, s) : tc_fp8_launch(L, s);
+        return p.base == GF2_BASE_TC_S8 ? tc_s8_launch(L, s)
+               : p.base == GF2_BASE_TC_B1 ? tc_b1_launch(L, s) : tc_fp8_launch(L, s);
     }
     M4rmLaunch L;
     L.A = A; L.lda = lda; L.bsA = bsA;
@@ -290,7 +307,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         GF2_CUDA_TRY(cudaMemset2DAsync(C->data, C->stride_words * 8, 0, words_of(n) * 8, m, s));
         return GF2_OK;
     }
-    const bool tc = (p.base == GF2_BASE_TC_FP8 || p.base == GF2_BASE_TC_S8);
+    const bool tc = is_tc(p.base);
     const uint64_t *Bsrc = B->data;
     int64_t ldBsrc = B->stride_words;
     const int d = p.depth;
@@ -836,7 +853,7 @@ int gf2_profile_read(int32_t family, double *ms, int64_t *launches)
 const char *gf2_profile_name(int32_t family)
 {
     static const char *names[PF_COUNT] = {"m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose",
-                                          "random", "freivalds", "make_table", "batched", "tc_s8"};
+                                          "random", "freivalds", "make_table", "batched", "tc_s8", "tc_b1"};
     if (family < 0 || family >= PF_COUNT) return nullptr;
     return names[family];
 }

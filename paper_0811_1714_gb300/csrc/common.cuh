@@ -40,7 +40,7 @@ void note_launch(int n = 1);
 
 // Kernel families for the device-time accounting of gf2_profile_*.
 enum ProfFamily { PF_M4RM = 0, PF_TC, PF_SPLIT, PF_COMBINE, PF_TRANSPOSE, PF_RANDOM, PF_MATVEC,
-                  PF_TABLE, PF_BATCHED, PF_TC_S8, PF_COUNT };
+                  PF_TABLE, PF_BATCHED, PF_TC_S8, PF_TC_B1, PF_COUNT };
 
 // Brackets the launches made during its lifetime with CUDA events on `s`
 // when accounting is on.
@@ -133,6 +133,8 @@ struct TcLaunch {
 };
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
 int tc_s8_launch(const TcLaunch &L, cudaStream_t s);
+// Binary tensor-core base case (mma.sync .b1 .and.popc on the packed words).
+int tc_b1_launch(const TcLaunch &L, cudaStream_t s);
 // Cubic product (Section 2.3) for at most 64 columns of C: BT = the n
 // columns of B as rows, 64 rows (rows n..63 zero), stride ldbt words.
 int cubic_narrow_launch(const uint64_t *A, int64_t lda, int64_t m, int64_t l, const uint64_t *BT,

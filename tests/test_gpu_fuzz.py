@@ -45,8 +45,8 @@ def with_garbage(X, cols, extra, rng):
 
 CASES = []
 _r = np.random.default_rng(20260)
-for _i in range(36):
-    base = [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_S8][_i % 3]
+for _i in range(40):
+    base = [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_S8, g.GF2_BASE_TC_B1][_i % 4]
     depth = int(_r.integers(0, 3))
     m, l, n = (int(x) for x in _r.integers(1, 2600, size=3))
     if depth:
