@@ -32,12 +32,29 @@ METRIC = "effective GF(2) bit-ops/s (2mnk/t) at n=32768, bit-exact"
 
 # DRAM traffic of the dominant kernel from an ncu capture of it (see
 # profiles/m4rm_kernel_n16384_depth2.md): bytes read + written per byte of leaf
-# operands (A, B, C slabs), valid while the kernel sources hash to "sha".
+# operands (A, B, C slabs), valid while the code of the kernel sources (comments
+# and blank lines removed) hashes to "sha".
 NCU_TRAFFIC = {
-    "m4rm": {"sha": "459f362071b4ddff", "sources": ["paper_0811_1714_gb300/csrc/m4rm.cu",
-                                         "paper_0811_1714_gb300/csrc/m4rm_dev.cuh"],
+    "m4rm": {"sha": "1e46ef05f46c7c8d", "sources": ["paper_0811_1714_gb300/csrc/m4rm.cu",
+                                                  "paper_0811_1714_gb300/csrc/m4rm_dev.cuh"],
              "bytes_per_operand_byte": 0.8845},
 }
+
+
+def code_sha(paths):
+    """sha256 prefix of the sources' code: // and /* */ comments, trailing
+    blanks and empty lines removed, so that editing a comment keeps a capture
+    valid and any change to the code does not."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in paths:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = (re.sub(r"//.*", "", ln).rstrip() for ln in text.splitlines())
+        h.update("\n".join(ln for ln in lines if ln).encode())
+    return h.hexdigest()[:16]
 
 
 # int8 warp-level tensor rate (mma.sync m16n8k32 .s8, dense) measured on a GB300
@@ -50,18 +67,13 @@ B1_MMA_SYNC_TOPS = 146.2
 
 def ncu_traffic(fam, leaves, M, L, N):
     """Per-launch DRAM bytes scaled from the capture, or None if the kernel changed."""
-    import hashlib
     ent = NCU_TRAFFIC.get(fam)
     if not ent:
         return None
-    h = hashlib.sha256()
     try:
-        for f in ent["sources"]:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
+        if code_sha(ent["sources"]) != ent["sha"]:
+            return None
     except OSError:
-        return None
-    if h.hexdigest()[:16] != ent["sha"]:
         return None
     return ent["bytes_per_operand_byte"] * leaves * (M * L + L * N + M * N) / 8.0
 UNIT = "bit-ops/s"

@@ -18,7 +18,9 @@
 //  * a table is built by the Gray-code walk of Section 3.1 in registers: a
 //    thread holds the combination of the high bits of the index and walks
 //    the low 4 bits in Gray order, one row addition (4 x 32-bit XOR) per new
-//    entry, so the whole table costs 2^k - 1 row additions as in the paper;
+//    entry; 16 threads fill a k = 8 table chunk in parallel, at 272 row
+//    additions against the paper's 2^k - 1 = 255 (the 16 high combinations
+//    are formed directly);
 //  * lookups: 8 lanes share one C row (16 bytes = 128 columns each), so a
 //    warp updates 4 rows per 128-bit shared-memory load; all accesses of a
 //    quarter-warp fall in one 128-byte table row (conflict free).

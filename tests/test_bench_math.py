@@ -73,3 +73,21 @@ def test_tc_roofline_counts_dense_flops_against_twice_bf16():
     assert r["peak"] == pytest.approx(3792.2)
     assert r["achieved"] == pytest.approx(2.0 * 4096 ** 3 * 343 / 21.5e-3 / 1e12)
     assert round(r["frac"], 2) == 0.58
+
+
+def test_code_sha_ignores_comments_but_not_code(tmp_path):
+    """The key that keeps a DRAM-traffic capture valid follows the kernel's
+    code only: comment and blank-line edits keep it, code edits change it."""
+    a = tmp_path / "a.cu"
+    b = tmp_path / "b.cu"
+    c = tmp_path / "c.cu"
+    a.write_text("// header\nint f(int x) { return x ^ 1; }  // tail\n")
+    b.write_text("/* another\n   header */\n\nint f(int x) { return x ^ 1; }\n")
+    c.write_text("// header\nint f(int x) { return x ^ 3; }  // tail\n")
+    assert bench.code_sha([str(a)]) == bench.code_sha([str(b)])
+    assert bench.code_sha([str(a)]) != bench.code_sha([str(c)])
+
+
+def test_recorded_traffic_key_matches_the_kernel_sources():
+    ent = bench.NCU_TRAFFIC["m4rm"]
+    assert bench.code_sha(ent["sources"]) == ent["sha"]
