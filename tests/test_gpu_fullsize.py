@@ -57,7 +57,7 @@ def check_product(m, l, n, base, p=0.5, seeds=(1, 2), blocks=4, depth=-1):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("base", [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8])
+@pytest.mark.parametrize("base", [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_S8, g.GF2_BASE_TC_B1])
 def test_square_32768(base):
     check_product(32768, 32768, 32768, base)
 
