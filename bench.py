@@ -134,8 +134,10 @@ def aggregate(ms_local, ops_local):
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi samples (every 20 ms, time-stamped) of SM clock and throttle
+    reasons.  Started before the warm-up so that it is running when the timed
+    region begins; summary(t0, t1) keeps the samples taken inside it."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -148,7 +150,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-i", str(self.gpu), "-lms", "100"],
+                 "-i", str(self.gpu), "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -165,27 +167,42 @@ class ClockSampler:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
         return False
 
-    def summary(self):
-        if not self.lines:
-            return None
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    def summary(self, t0=None, t1=None):
+        """Median SM clock, max clock and throttle reasons of the samples taken
+        between host times t0 and t1 (all samples when none fall inside)."""
+        import datetime
+        rows = []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
+        window = "timed region"
+        if t0 is not None and t1 is not None:
+            inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+            if inside:
+                rows = inside
+            else:
+                window = "whole run (no sample inside the timed region)"
+        else:
+            window = "whole run"
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, _, flags in rows:
+            for nm, v in zip(names, flags):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "window": window}
 
 
 # ---------------------------------------------------------------- our arm
@@ -287,23 +304,25 @@ def run_ours(args, rank, world, local_rank):
             results[path] = {"unavailable": str(e)}
             continue
         torch.cuda.synchronize()
-        for _ in range(args.warmup):
-            g.gf2_mul(MC, MA, MB, o)
-        torch.cuda.synchronize()
-        plan = g.gf2_describe_plan(m, l, n, o)
-        if dist is not None:
-            dist.barrier()
-        launches0 = g.gf2_launch_count()
-        g.gf2_profile_enable(True)
         with ClockSampler(local_rank) as cs:
+            for _ in range(args.warmup):
+                g.gf2_mul(MC, MA, MB, o)
+            torch.cuda.synchronize()
+            plan = g.gf2_describe_plan(m, l, n, o)
+            if dist is not None:
+                dist.barrier()
+            launches0 = g.gf2_launch_count()
+            g.gf2_profile_enable(True)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
+            t_start = time.time()
             ev0.record(stream)
             for _ in range(args.steps):
                 g.gf2_mul(MC, MA, MB, o)
             ev1.record(stream)
             torch.cuda.synchronize()
+            t_end = time.time()
         ms_total = ev0.elapsed_time(ev1)
         launches = g.gf2_launch_count() - launches0
         fam = {}
@@ -338,7 +357,7 @@ def run_ours(args, rank, world, local_rank):
             "ms": ms, "value": value, "depth": d, "plan": plan, "hbm_kernels": hbm,
             "gpu_launches": launches, "kernels": fam, "dominant": dom,
             "dominant_ms_per_launch": dom_ms, "roofline": rl,
-            "freivalds_mismatched_rows": bad, "clocks": cs.summary(),
+            "freivalds_mismatched_rows": bad, "clocks": cs.summary(t_start, t_end),
         }
     ok = {p: r for p, r in results.items() if "ms" in r}
     if not ok:

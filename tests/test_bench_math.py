@@ -91,3 +91,27 @@ def test_code_sha_ignores_comments_but_not_code(tmp_path):
 def test_recorded_traffic_key_matches_the_kernel_sources():
     ent = bench.NCU_TRAFFIC["m4rm"]
     assert bench.code_sha(ent["sources"]) == ent["sha"]
+
+
+def test_clock_summary_keeps_the_timed_region():
+    """Samples outside [t0, t1] (the warm-up, the tail) are left out; a
+    throttle reason seen inside the region is reported."""
+    import datetime
+    base = datetime.datetime(2026, 12, 4, 3, 0, 0)
+
+    def line(dt_ms, mhz, pwr_cap="Not Active", hw="Not Active"):
+        ts = (base + datetime.timedelta(milliseconds=dt_ms)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return "%s, 0, %d, 2070, 900.0, 0x0, %s, Not Active, Not Active, %s" % (ts, mhz, hw, pwr_cap)
+
+    cs = bench.ClockSampler(0)
+    cs.lines = [line(0, 1200), line(20, 1300, hw="Active"),               # warm-up
+                line(100, 2070), line(120, 2055, pwr_cap="Active"), line(140, 2070),
+                line(300, 1000)]                                        # after the region
+    t0 = (base + datetime.timedelta(milliseconds=90)).timestamp()
+    t1 = (base + datetime.timedelta(milliseconds=150)).timestamp()
+    s = cs.summary(t0, t1)
+    assert s["samples"] == 3 and s["window"] == "timed region"
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"]
+    whole = cs.summary()
+    assert whole["samples"] == 6 and "hw_slowdown" in whole["reasons"]
