@@ -4,10 +4,16 @@
 // Section 3, Algorithms 1-3).
 //
 // Device side: a persistent kernel whose CTAs pull tiles from one atomic
-// work counter.  A tile is (product, first row, first word) of a C block of
-// BM rows x LPR*128 columns; every product has its own A, B, C pointers,
-// strides and sizes in a descriptor table.  Tiles are ordered by decreasing
-// K extent (longest first) so the queue drains evenly.
+// work counter.  Every product has its own A, B, C pointers, strides and
+// sizes in a descriptor table.  Two kinds of tile:
+//  * one product per tile: (product, first row, first word) of a C block of
+//    BM rows x LPR*128 columns (m4rm_batched_kernel);
+//  * slot-packed: the 8 sixteen-byte lane chunks of a 1024-column tile are
+//    128-column slices of up to 8 different products, each lane working on
+//    its own slot's A rows, B rows, masks and C (m4rm_slots_kernel), so that
+//    narrow products do not leave most of a tile empty.
+// Tiles are ordered by decreasing K extent (longest first) so the queue
+// drains evenly.
 //
 // Host side (gf2_mul_batched): the first call for a set of operands builds
 // the descriptor tables, lets the autotuner time every candidate variant on

@@ -4,8 +4,10 @@
 // so these kernels are pure HBM streams: read the four quadrants of each
 // parent once, write the seven product operands (split), or read the seven
 // products and write the four quadrants of the parent (combine).  They run
-// breadth first, one launch per recursion level for all 7^j sub-problems of
-// that level, so the GPU stays full at every level.  Operands below the top
+// breadth first, one launch for all 7^j sub-problems of a level, so the GPU
+// stays full at every level; two levels are fused per launch while two
+// remain (sw_split2 / sw_combine2: 16 sub-blocks in, 49 operands out, and
+// back, the middle level never leaving registers).  Operands below the top
 // level live in dense slabs of the scratch arena (the "copy out" of
 // Section 4 happens for all three matrices, which keeps every leaf product
 // contiguous).
