@@ -1,6 +1,9 @@
 // api.cu -- the C ABI of libgf2: argument checks, the Strassen-Winograd
-// plan (Section 4, Algorithm 4) with its scratch arena, dispatch to the base
-// cases, host staging, and Freivalds' check.
+// plan (Section 4, Algorithm 4) with its per-(device, stream) scratch arena,
+// dispatch to the base cases, odd sizes by virtual padding or by peeling
+// (Section 4), the autotuner's choice of base case x depth and of padding vs
+// peeling (timed on the caller's operands, cached per shape), host staging,
+// the batched entry point, and Freivalds' check.
 #include "common.cuh"
 
 #include <algorithm>

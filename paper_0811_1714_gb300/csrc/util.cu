@@ -1,5 +1,8 @@
-// util.cu -- device helpers: seeded bit generator, bit transpose, the packed
-// matrix-vector product used by Freivalds' check, launch bookkeeping.
+// util.cu -- device helpers: seeded bit generator, bit transpose (optionally
+// with bit-reversed 32-bit halves, the FP8 base case's order), the packed
+// matrix-vector product used by Freivalds' check, the cubic product of
+// Section 2.3 for right factors of at most 64 columns, launch bookkeeping and
+// device-time accounting.
 #include "common.cuh"
 
 #include <atomic>
