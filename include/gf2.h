@@ -113,7 +113,9 @@ int gf2_free(gf2_mat *M);
 /* ---- the product ---------------------------------------------------------
  * C = A B  (or C ^= A B with opts->accumulate), A m x l, B l x n, C m x n.
  * Section 4 (Algorithm 4) recursion to opts->depth levels -- operands are
- * zero-padded virtually to even, word-aligned sizes (Section 4, "padding")
+ * zero-padded virtually to even, word-aligned sizes (Section 4, "padding"),
+ * or with opts->peel the largest evenly halving core recurses and the
+ * leftover rows, columns and K entries are base-case products ("peeling")
  * -- then the base case of opts->base on all 7^depth leaf products at once.
  * Temporaries live in the scratch arena of (device, stream).  opts may be
  * NULL (defaults).  C must not overlap A or B (GF2_EALIAS).  Zero-sized
