@@ -63,6 +63,22 @@ S8_MMA_SYNC_TOPS = 150.3
 # binary warp-level tensor rate (mma.sync m16n8k256 .b1 .and.popc: AND + popcount
 # per bit pair), measured the same way: the peak for the binary base case.
 B1_MMA_SYNC_TOPS = 146.2
+# shared-memory read bandwidth of all 152 SMs measured on a GB300 at 2070 MHz by a
+# probe with the M4RM lookup pattern (each quarter-warp reads one 128-byte row as
+# 8 x 16 bytes, four independent rows in flight per thread): 121.5 B/clk/SM, 95 %
+# of the nominal 128 B/clk (152 x 128 B x 2070 MHz = 40.3 TB/s).  The peak for
+# the packed M4RM base cases.
+SMEM_LOOKUP_GBS = 38200.0
+
+
+def smem_peak(peaks):
+    """(peak GB/s, note) of shared-memory reads: the measured lookup-pattern
+    rate, scaled when the clock differs from the 2070 MHz it was taken at."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = SMEM_LOOKUP_GBS * mhz / 2070.0
+    return peak, ("measured shared-memory read rate with the lookup pattern, %.1f TB/s "
+                  "(nominal 152 SMs x 128 B/clk x %.0f MHz = %.1f TB/s)" %
+                  (peak / 1000.0, mhz, 152 * 128 * mhz / 1e6))
 
 
 def ncu_traffic(fam, leaves, M, L, N):
@@ -236,12 +252,11 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
     # packed M4RM: table-row reads from shared memory, M*L*N/(8k) bytes per product
     smem_bytes = M * L * N / (8.0 * k) * leaves
     achieved = smem_bytes / (ms_per_launch * 1e-3) / 1e9
-    peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+    peak, note = smem_peak(peaks)
     return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": ncu_traffic("m4rm", leaves, M, L, N),
             "traffic_note": "DRAM bytes per launch, scaled by leaf operand bytes from a 49-leaf ncu capture",
-            "peak_note": "152 SMs x 128 B/clk x %.0f MHz (shared-memory bandwidth)" %
-                         peaks.get("sm_max_mhz", 2070.0)}
+            "peak_note": note}
 
 
 def strassen_stream_bytes(M, L, N, d):
@@ -520,10 +535,10 @@ def run_batched(args, rank, world, local_rank):
         per_launch_ms = k_ms / k_n
         smem_bytes = sum(m * l * n for m, l, n in dims) / (8.0 * kbits)
         achieved = smem_bytes / (per_launch_ms * 1e-3) / 1e9
-        peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+        peak, note = smem_peak(peaks)
         rl = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
               "traffic": None, "kernel_ms_per_launch": per_launch_ms,
-              "peak_note": "152 SMs x 128 B/clk x %.0f MHz (shared-memory bandwidth)" % peaks.get("sm_max_mhz", 2070.0),
+              "peak_note": note,
               "work_note": "table-row reads of k=%d tables, sum of m*l*n/(8k) over the 4096 products" % kbits}
     ms, ops_all, value = aggregate(ms_local, ops)
     # the same batch on the tensor-core base case: one batched transpose and
