@@ -12,11 +12,19 @@ Matrices are passed as :class:`Mat` (the C ``gf2_mat``), made from
 * a host numpy ``uint64`` array or torch CPU tensor of the same shape
   (device ``GF2_HOST``; pinned memory gives full copy speed).
 
-Entry points keep the C names: ``gf2_alloc``, ``gf2_free``, ``gf2_mul``,
-``gf2_mul_batched``, ``gf2_sw_split``, ``gf2_sw_combine``,
-``gf2_make_table``, ``gf2_random``, ``gf2_transpose``, ``gf2_freivalds``,
-``gf2_scratch_bytes``, ``gf2_reserve_scratch``, ``gf2_release_scratch``,
-``gf2_launch_count``, ``gf2_describe_plan``, ``gf2_strerror``.
+Entry points keep the C names of every symbol in ``include/gf2.h`` (listed in
+:data:`EXPORTS`): the product (``gf2_mul``, ``gf2_mul_batched``,
+``gf2_mul_batched_ex``, ``gf2_mul_noalloc``), memory (``gf2_alloc``,
+``gf2_free``), the steps of the path callable alone (``gf2_sw_split``,
+``gf2_sw_combine``, ``gf2_make_table``), helpers (``gf2_random``,
+``gf2_transpose``, ``gf2_freivalds``), scratch control, planning
+(``gf2_describe_plan``), device-time accounting (``gf2_profile_*``) and
+failure detection (``gf2_device_status``, ``gf2_selftest_wait``).
+
+Base cases (``opts(base=...)``): ``GF2_BASE_AUTO`` (the autotuner's choice),
+``GF2_BASE_M4RM`` (packed Method of the Four Russians), ``GF2_BASE_TC_FP8``
+(exact 0/1 FP8 tcgen05 products), and the warp-level ``GF2_BASE_TC_S8``
+(int8) and ``GF2_BASE_TC_B1`` (1-bit AND + popcount) forms.
 """
 from __future__ import annotations
 
