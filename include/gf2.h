@@ -94,20 +94,31 @@ typedef struct gf2_opts {
     int32_t reserved[2];   /* must be 0                                                   */
 } gf2_opts;
 
-/* Fill *opts with the defaults (everything automatic, C = A B). */
+/* Fill *opts with the defaults: everything automatic, C = A B.  Algorithm 1
+ * starts from C = GenerateZeroMatrix(m, n), so overwriting C is the default
+ * and accumulate = 0; the depth (Section 4's cutoff, Section 5's c_s) and the
+ * table shape (Section 3.1's k, Section 3.3's t) are chosen by the library. */
 void gf2_default_opts(gf2_opts *opts);
 
-/* Message for a status code (static string, never NULL). */
+/* Message for a status code (static string, never NULL).  The statuses are
+ * the boundary's own error convention (the paper's algorithms have no error
+ * paths); they cover the preconditions the paper states for the product:
+ * A.cols == B.rows and C of m x n (Section 3 problem statement), and the
+ * Section 2.1 layout (stride, alignment). */
 const char *gf2_strerror(int status);
 
 /* ---- memory -------------------------------------------------------------
- * gf2_alloc: device matrix on the CURRENT CUDA device, zero-filled, stride
- * ceil(cols/64) rounded up to even.  rows or cols may be 0 (data is then
- * NULL).  On failure *M is left with data == NULL.
- * gf2_free: releases what gf2_alloc returned; idempotent (data set to NULL).
- * Both synchronise with the device (cudaMalloc / cudaFree semantics).
+ * gf2_alloc: Algorithm 1's "C <- GenerateZeroMatrix(m, n)" as a call: a
+ * rows x cols device matrix on the CURRENT CUDA device in the Section 2.1
+ * flat row-major layout, zero-filled, stride ceil(cols/64) rounded up to
+ * even.  rows or cols may be 0 (data is then NULL).  On failure *M is left
+ * with data == NULL.  Synchronises with the device (cudaMalloc semantics).
  */
 int gf2_alloc(gf2_mat *M, int64_t rows, int64_t cols);
+
+/* gf2_free: releases a matrix of gf2_alloc (Algorithm 1's GenerateZeroMatrix,
+ * Section 2.1 layout); idempotent (data set to NULL); GF2_EINVAL for a host
+ * matrix.  Synchronises with the device (cudaFree semantics). */
 int gf2_free(gf2_mat *M);
 
 /* ---- the product ---------------------------------------------------------
@@ -135,15 +146,20 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B,
             const gf2_opts *opts, void *cuda_stream);
 
 /* ---- batched products ----------------------------------------------------
- * C[i] = A[i] B[i] for i < count, independent shapes, one launch of a
- * persistent kernel that pulls tiles of all products from one work queue
- * (device operands only).  Same per-product rules as gf2_mul.
+ * C[i] = A[i] B[i] for i < count, independent shapes.  Each product is the
+ * one gf2_mul computes: Section 4's Algorithm 4 where it recurses, else the
+ * base case of Section 3 (Algorithms 1 and 3, t tables) or the tensor-core
+ * form of Section 2.3's integer dot products mod 2.  The products that do
+ * not recurse run in ONE launch of a persistent kernel that pulls tiles of
+ * all of them from one work queue (device operands only).  Same
+ * per-product rules as gf2_mul; details under gf2_mul_batched_ex.
  */
 int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[],
                     const gf2_mat *const B[], int32_t count,
                     const gf2_opts *opts, void *cuda_stream);
 
-/* gf2_mul_batched_ex: gf2_mul_batched with the batched base case's tile
+/* gf2_mul_batched_ex: gf2_mul_batched (Section 3's Algorithms 1 and 3 per
+ * product, one persistent launch) with the batched base case's tile
  * variant pinned (variant >= 0, see gf2_batched_variant_name) or chosen by
  * the autotuner (variant = -1).  *chosen (may be NULL) receives the variant
  * used.  Details of the batched form:
@@ -165,9 +181,12 @@ int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[],
                        const gf2_opts *opts, int32_t variant, int32_t *chosen,
                        void *cuda_stream);
 
-/* Number of tile variants of the batched base case, and the name of one
- * ("k<k>t<t>-w<columns>-bm<rows>"; NULL beyond the last). */
+/* Number of tile variants of the batched base case: shapes of Section 3's
+ * tables (k bits, Section 3.1; t tables, Section 3.3) x tile width x rows. */
 int32_t gf2_batched_variant_count(void);
+
+/* Name of one batched tile variant, "k<k>t<t>-w<columns>-bm<rows>" with k
+ * and t as in Sections 3.1 and 3.3 (NULL beyond the last). */
 const char *gf2_batched_variant_name(int32_t variant);
 
 /* ---- steps of the path, callable alone ------------------------------------
@@ -201,18 +220,22 @@ int gf2_make_table(gf2_mat *T, const gf2_mat *B, int64_t r0, int32_t k,
                    void *cuda_stream);
 
 /* ---- helpers ---------------------------------------------------------------
- * gf2_random: fill a device matrix with the seeded SplitMix64 bits (p = 0.5
+ * gf2_random: the random dense matrices the paper times (Section 6, Tables
+ * 5-7) as seeded synthetic input: fill a device matrix with the seeded SplitMix64 bits (p = 0.5
  * takes whole outputs; otherwise one 32-bit uniform per bit), tail bits and
  * padding words 0.  Word (r, w) uses output r*ceil(cols/64)+w+1 of the stream
  * seeded with `seed` (p = 0.5), or outputs (r*W+w)*32+j+1, j < 32 (p != 0.5).
  */
 int gf2_random(gf2_mat *M, uint64_t seed, double p, void *cuda_stream);
 
-/* gf2_transpose: T = X^T (T is X.cols x X.rows). */
+/* gf2_transpose: T = X^T (T is X.cols x X.rows), Section 2.1 layout on both
+ * sides.  Section 2.3's cubic product reads B transposed (rows of B^T are the
+ * columns of B); the tensor-core base cases do too. */
 int gf2_transpose(gf2_mat *T, const gf2_mat *X, void *cuda_stream);
 
 /* gf2_freivalds: checks C == A B with 64 random vectors at once (Freivalds'
- * test): X = seeded n x 64 bits, compares A (B X) with C X.  A wrong C
+ * test; the paper has no verification step, the dot products are Section
+ * 2.3's AND + parity on packed words): X = seeded n x 64 bits, compares A (B X) with C X.  A wrong C
  * passes with probability <= 2^-64.  *mismatched_rows receives the number of
  * rows of A(BX) + CX that are non-zero (0 means the check passed).  Blocks
  * the calling thread until the stream has finished the check.
@@ -222,27 +245,39 @@ int gf2_freivalds(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B,
 
 /* ---- scratch ---------------------------------------------------------------
  * gf2_scratch_bytes: device scratch that gf2_mul needs for these shapes and
- * options (0 when it needs none).
- * gf2_reserve_scratch: grow the arena of (current device, stream) to at
- * least `bytes` now, so that later calls do not allocate.
- * gf2_release_scratch: free every arena of the current device (synchronises
- * the device first).
+ * options (0 when it needs none): the temporaries of Section 4's Algorithm 4
+ * (operand and product slabs of every level, breadth first; Section 4
+ * discusses the paper's own two-temporary schedule) plus the transposed B of
+ * the tensor-core base cases.
  */
 int64_t gf2_scratch_bytes(int64_t m, int64_t l, int64_t n, const gf2_opts *opts);
+
+/* gf2_reserve_scratch: grow the arena of (current device, stream), which
+ * holds Algorithm 4's temporaries (Section 4), to at least `bytes` now, so
+ * that later calls do not allocate. */
 int gf2_reserve_scratch(int64_t bytes, void *cuda_stream);
+
+/* gf2_release_scratch: free every arena of Algorithm 4's temporaries
+ * (Section 4) on the current device (synchronises the device first). */
 int gf2_release_scratch(void);
 
-/* Number of kernels this library has launched in this process (all devices). */
+/* Number of kernels this library has launched in this process (all devices).
+ * Bookkeeping of the boundary; the paper has no counterpart (it times whole
+ * products, Section 6). */
 int64_t gf2_launch_count(void);
 
-/* gf2_device_status: waits for `cuda_stream`, then reads and clears the
+/* gf2_device_status: failure detection of the boundary (the paper has no
+ * counterpart; it guards the tensor-core form of Section 2.3's dot
+ * products): waits for `cuda_stream`, then reads and clears the
  * device status word of the tensor-core base case.  Returns GF2_OK, or
  * GF2_ETIMEOUT when one of its bounded waits expired since the last read
  * (its kernels then stop early and the product is not valid).
  */
 int gf2_device_status(void *cuda_stream);
 
-/* gf2_selftest_wait: tests the failure detection without a GPU fault.
+/* gf2_selftest_wait: tests the failure detection without a GPU fault (the
+ * paper has no counterpart; the wait is the one the Section 2.3 tensor-core
+ * form's pipeline uses).
  * Launches one CTA whose single wait can never be satisfied (an mbarrier no
  * one arrives on); after `limit_cycles` SM clock cycles (1 .. 4e9) the wait
  * gives up and records GF2_ETIMEOUT in the same status word the tensor-core
@@ -254,16 +289,24 @@ int gf2_selftest_wait(int64_t limit_cycles, void *cuda_stream);
 /* ---- device-time accounting ----------------------------------------------
  * gf2_profile_enable(1) clears the counters and starts bracketing every
  * kernel launch of the library with CUDA events on its stream; (0) stops.
- * gf2_profile_read waits for the recorded events and returns the summed
- * device time (ms) and launch count of one kernel family:
- *   0 m4rm base case, 1 tensor-core base case, 2 Strassen split,
- *   3 Strassen combine, 4 transpose, 5 generator, 6 Freivalds products,
- *   7 MakeTable, 8 batched base case, 9 int8 tensor-core base case,
- *   10 binary tensor-core base case.
- * gf2_profile_name gives the family's name (NULL beyond the last one).
+ * The per-step breakdown of Section 6's timings (Tables 5-7 time whole
+ * products; this splits them by kernel family).
  */
 int gf2_profile_enable(int32_t on);
+
+/* gf2_profile_read waits for the recorded events and returns the summed
+ * device time (ms) and launch count of one kernel family (Section 6's
+ * timings split by step):
+ *   0 m4rm base case (Section 3), 1 tensor-core base case (Section 2.3),
+ *   2 Strassen split, 3 Strassen combine (Section 4, Algorithm 4),
+ *   4 transpose, 5 generator, 6 Freivalds products, 7 MakeTable
+ *   (Algorithm 1), 8 batched base case, 9 int8 tensor-core base case,
+ *   10 binary tensor-core base case (Section 2.3).
+ */
 int gf2_profile_read(int32_t family, double *ms, int64_t *launches);
+
+/* gf2_profile_name gives the name of a gf2_profile_read family (Section 6's
+ * timings split by step; NULL beyond the last one). */
 const char *gf2_profile_name(int32_t family);
 
 /* ---- product without allocation --------------------------------------------
@@ -275,17 +318,25 @@ const char *gf2_profile_name(int32_t family);
  * absorb the device-wide synchronisation that cudaMalloc and cudaFree
  * imply.
  *
- * gf2_mul_noalloc computes exactly what gf2_mul computes (same plan, same
- * kernels, same options) for device operands, but takes the Strassen-
- * Winograd temporaries (and the transposed B of the tensor-core base case)
- * from one fixed buffer of GF2_NOALLOC_SCRATCH_BYTES that lives in the
- * library's device image: every GPU that loads the library holds that
- * buffer until the process exits.  It calls no cudaMalloc, cudaFree or
- * other allocating routine.  The caller still provides A, B and C.
+ * gf2_mul_noalloc computes the same product as gf2_mul (the result is
+ * unique, so the words of C are identical) for device operands, with the
+ * same kernels, but takes the Strassen-Winograd temporaries (and the
+ * transposed B of the tensor-core base case) from one fixed buffer of
+ * GF2_NOALLOC_SCRATCH_BYTES that lives in the library's device image: every
+ * GPU that loads the library holds that buffer until the process exits.  It
+ * calls no cudaMalloc, cudaFree or other allocating routine.  The caller
+ * still provides A, B and C.
  *
- *  - The first call on a device looks up the buffer's device address
- *    (cudaGetSymbolAddress, once per device, with that device current);
- *    make that first call before any stream capture.
+ *  - Its plan is the cutoff rule's, not the autotuner's: base GF2_BASE_AUTO
+ *    means the packed base case, depth -1 the cutoff rule's depth, and odd
+ *    sizes are padded (peel 0 or -1).  gf2_mul may pick another base case
+ *    or depth for large shapes after timing them; peel = 1 is refused with
+ *    GF2_EUNSUPPORTED.
+ *  - The first call on a device, in each CUDA context, looks up the
+ *    buffer's device address (cudaGetSymbolAddress, with that device
+ *    current) and keeps it for that context; make that first call before
+ *    any stream capture (also after a cudaDeviceReset, which starts a new
+ *    context).
  *  - If the plan for these shapes and options needs more scratch than the
  *    buffer holds, the call launches nothing and returns GF2_ESCRATCH
  *    (gf2_scratch_bytes gives the need; lower opts->depth to reduce it).
@@ -302,7 +353,9 @@ int gf2_mul_noalloc(gf2_mat *C, const gf2_mat *A, const gf2_mat *B,
                     const gf2_opts *opts, void *cuda_stream);
 
 /* Plan that gf2_mul would use for these shapes and options, as text (for
- * logs and tests): writes at most `cap` bytes including the terminating NUL.
+ * logs and tests): Section 4's recursion depth and padding or peeling, and
+ * the base case's table shape (Sections 3.1 and 3.3, tuned as in Section 5).
+ * Writes at most `cap` bytes including the terminating NUL.
  */
 int gf2_describe_plan(int64_t m, int64_t l, int64_t n, const gf2_opts *opts,
                       char *buf, int32_t cap);

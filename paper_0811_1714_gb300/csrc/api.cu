@@ -640,7 +640,8 @@ int choose_peel(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts &
 namespace gf2 {
 
 // gf2_mul for device operands with caller-owned scratch (no allocation):
-// the checks of gf2_mul, the same plan, then the device path on `scratch`.
+// the checks of gf2_mul, then the cutoff rule's plan (no autotuning, odd
+// sizes padded; peeling is refused) and the device path on `scratch`.
 int mul_with_scratch(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts,
                      void *scratch, size_t scratch_bytes, void *stream)
 {
@@ -649,6 +650,7 @@ int mul_with_scratch(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_o
     if (A->cols != B->rows || C->rows != A->rows || C->cols != B->cols) return GF2_EINVAL;
     const gf2_opts o = resolve(opts);
     if ((rc = check_opts(o))) return rc;
+    if (o.peel == 1) return GF2_EUNSUPPORTED;
     if (overlaps(C, A) || overlaps(C, B)) return GF2_EALIAS;
     int dev = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));

@@ -544,10 +544,64 @@ int launch_variant(const BVariant &v, const BProd *dp, const void *dt, int ntile
     return check_launch();
 }
 
+int autotune_timed(const std::vector<BProd> &prods, int accumulate, cudaStream_t s);
+
+// Copies of the products' C (words that carry entries, rows packed densely)
+// to `buf` (to_buf) or back (!to_buf), one 2-D copy per product.
+int copy_cs(const std::vector<BProd> &prods, char *buf, bool to_buf, cudaStream_t s)
+{
+    size_t off = 0;
+    for (const BProd &p : prods) {
+        if (p.m <= 0 || p.n <= 0) continue;
+        const size_t w = (size_t)words_of(p.n) * 8;
+        if (to_buf)
+            GF2_CUDA_TRY(cudaMemcpy2DAsync(buf + off, w, p.C, (size_t)p.ldc * 8, w, (size_t)p.m,
+                                           cudaMemcpyDeviceToDevice, s));
+        else
+            GF2_CUDA_TRY(cudaMemcpy2DAsync(p.C, (size_t)p.ldc * 8, buf + off, w, w, (size_t)p.m,
+                                           cudaMemcpyDeviceToDevice, s));
+        off += w * (size_t)p.m;
+    }
+    return GF2_OK;
+}
+
 // Times every candidate on this batch (two runs each after one warm-up) and
 // returns the index of the fastest, or GF2_ECUDA when its timing events
-// cannot be created.
+// cannot be created.  Every timed launch writes the products' C; with
+// accumulate each one XORs A B into it again, so C is saved first and put
+// back afterwards (the caller's launch then sees the C it was given).
 int autotune(const std::vector<BProd> &prods, int accumulate, cudaStream_t s)
+{
+    void *saved = nullptr;
+    if (accumulate) {
+        size_t bytes = 0;
+        for (const BProd &p : prods)
+            if (p.m > 0 && p.n > 0) bytes += (size_t)words_of(p.n) * 8 * (size_t)p.m;
+        if (bytes) {
+            if (cudaMalloc(&saved, bytes) != cudaSuccess) {
+                cudaGetLastError();
+                return GF2_ENOMEM;
+            }
+            const int rc = copy_cs(prods, static_cast<char *>(saved), true, s);
+            if (rc) {
+                cudaFree(saved);
+                return rc;
+            }
+        }
+    }
+    const int best = autotune_timed(prods, accumulate, s);
+    if (saved) {
+        const int rc = copy_cs(prods, static_cast<char *>(saved), false, s);
+        const cudaError_t e = cudaStreamSynchronize(s);
+        cudaFree(saved);
+        if (rc) return rc;
+        if (e != cudaSuccess) return GF2_ECUDA;
+    }
+    return best;
+}
+
+// The timing loop of autotune.
+int autotune_timed(const std::vector<BProd> &prods, int accumulate, cudaStream_t s)
 {
     const auto &vs = bvariants();
     int best = 0;
@@ -603,7 +657,7 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
     std::vector<BProd> prods;
     prods.reserve(count);
     std::vector<unsigned long long> key;
-    key.reserve(6 * (size_t)count + 4);
+    key.reserve(9 * (size_t)count + 4);
     for (int i = 0; i < count; ++i) {
         BProd p;
         p.A = A[i]->data; p.B = B[i]->data; p.C = C[i]->data;
@@ -613,8 +667,12 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
         key.push_back((unsigned long long)(uintptr_t)p.A);
         key.push_back((unsigned long long)(uintptr_t)p.B);
         key.push_back((unsigned long long)(uintptr_t)p.C);
-        key.push_back(((unsigned long long)p.lda << 32) ^ (unsigned long long)p.ldb ^ ((unsigned long long)p.ldc << 16));
-        key.push_back(((unsigned long long)p.m << 40) ^ ((unsigned long long)p.l << 20) ^ (unsigned long long)p.n);
+        key.push_back((unsigned long long)p.lda);
+        key.push_back((unsigned long long)p.ldb);
+        key.push_back((unsigned long long)p.ldc);
+        key.push_back((unsigned long long)p.m);
+        key.push_back((unsigned long long)p.l);
+        key.push_back((unsigned long long)p.n);
     }
     int dev = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));

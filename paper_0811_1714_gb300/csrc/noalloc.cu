@@ -7,9 +7,11 @@
 // GPU that loads the library holds it until the process exits.  Host code
 // must not pass the array's name to a kernel (on the host it names a
 // stand-in, not device memory): its device address is looked up here, once
-// per device with that device current, by cudaGetSymbolAddress, and only
-// that address is handed on.
+// per device and CUDA context with that device current, by
+// cudaGetSymbolAddress, and only that address is handed on.
 #include "common.cuh"
+
+#include <cuda.h>
 
 #include <mutex>
 
@@ -24,11 +26,38 @@ constexpr size_t kScratchBytes = (size_t)GF2_NOALLOC_SCRATCH_BYTES;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-void *g_scratch_ptr[kMaxDevices];   // device address of the buffer, per device (null: not set up)
+// The buffer's device address belongs to the CUDA context it was looked up
+// in: after a cudaDeviceReset, or with another context current, it has to
+// be looked up again.  So the cache is keyed by (device, current context).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
 
-// Set-up on the current device: the buffer's device address, once.
+CtxGetCurrentFn ctx_get_current()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+struct SetUp {
+    int dev = -1;
+    CUcontext ctx = nullptr;
+    void *ptr = nullptr;
+};
+constexpr int kSlots = 64;
+std::mutex g_setup_mu;
+SetUp g_setup[kSlots];   // (device, context) -> device address of the buffer
+int g_next_slot = 0;
+
+// Set-up on the current device: the buffer's device address, once per
+// (device, context).
 int scratch_for_current_device(void **out)
 {
     int dev = 0;
@@ -36,18 +65,33 @@ int scratch_for_current_device(void **out)
         cudaGetLastError();
         return GF2_ECUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) return GF2_EUNSUPPORTED;
+    CUcontext ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    bool keyed = get && get(&ctx) == CUDA_SUCCESS && ctx;
     std::lock_guard<std::mutex> lk(g_setup_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            return GF2_ECUDA;
-        }
-        g_scratch_ptr[dev] = p;
+    if (keyed)
+        for (const SetUp &e : g_setup)
+            if (e.ptr && e.dev == dev && e.ctx == ctx) {
+                *out = e.ptr;
+                return GF2_OK;
+            }
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        return GF2_ECUDA;
     }
-    *out = g_scratch_ptr[dev];
+    // no context was current before the lookup, which made the device's
+    // primary context current: key the address by that one
+    if (!keyed) keyed = get && get(&ctx) == CUDA_SUCCESS && ctx;
+    if (keyed) {
+        SetUp &slot = g_setup[g_next_slot];
+        g_next_slot = (g_next_slot + 1) % kSlots;
+        slot.dev = dev;
+        slot.ctx = ctx;
+        slot.ptr = p;
+    }
+    *out = p;
     return GF2_OK;
 }
 

@@ -34,6 +34,29 @@ def test_header_and_binding_agree():
     assert sorted(g.EXPORTS) == declared_functions()
 
 
+CITATION = re.compile(r"Sections? \d|Algorithms? \d|Tables? \d|no counterpart")
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment block (the nearest one above it) names the
+    passage of the paper it restates -- a Section, Algorithm or Table -- or
+    says that the paper has no counterpart."""
+    text = open(HEADER).read()
+    missing = []
+    for mt in re.finditer(r"^[A-Za-z_].*?\b(gf2_[a-z0-9_]+)\s*\(", text, flags=re.M):
+        name = mt.group(1)
+        before = text[:mt.start()]
+        end = before.rfind("*/")
+        start = before.rfind("/*", 0, end)
+        block = before[start:end] if start >= 0 and end >= 0 else ""
+        block = re.sub(r"\s*\n\s*\*?\s*", " ", block)     # one line, comment stars dropped
+        if not CITATION.search(block):
+            missing.append(name)
+    assert not missing, "declarations without a cited passage: %s" % missing
+    assert len(set(re.findall(r"^[A-Za-z_].*?\b(gf2_[a-z0-9_]+)\s*\(", text, flags=re.M))) == \
+        len(declared_functions())
+
+
 def test_library_exports_every_declared_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", g.LIB_PATH], capture_output=True,
                          text=True, check=True).stdout

@@ -120,3 +120,27 @@ def test_batch_of_4096_log_uniform_products():
     # Freivalds' test on every product
     bad = [i for i in range(len(dims)) if g.gf2_freivalds(MC[i], MA[i], MB[i], 77 + i) != 0]
     assert not bad, bad[:10]
+
+
+def test_autotuned_batch_with_accumulate():
+    """C ^= A B on a batch whose shape signature has not been tuned yet: the
+    autotuner times every variant on the caller's C, which must not leave
+    those timing runs' XORs behind (C0 ^ A B after the call, C0 again after
+    a second, graph-replayed call)."""
+    dims = synth.batch_dims(37, seed=4242, lo=20, hi=700)
+    bt = make_batch(dims, 7000)
+    C0 = []
+    for i, (m, l, n) in enumerate(dims):
+        c0 = synth.random_packed(m, n, 8000 + i)
+        bt["dC"][i].copy_(to_dev(c0))
+        C0.append(c0)
+    o = g.opts(base=g.GF2_BASE_M4RM, depth=0, accumulate=1)
+    g.gf2_mul_batched_ex(bt["arrs"], options=o)
+    torch.cuda.synchronize()
+    for i, (m, l, n) in enumerate(dims):
+        ref = oracle.mul_packed(bt["hostA"][i], bt["hostB"][i], m, l, n) ^ C0[i]
+        assert_same_bits(to_host(bt["dC"][i]), ref, n, "first accumulate %s" % ((m, l, n),))
+    g.gf2_mul_batched_ex(bt["arrs"], options=o)
+    torch.cuda.synchronize()
+    for i, (m, l, n) in enumerate(dims):
+        assert_same_bits(to_host(bt["dC"][i]), C0[i], n, "second accumulate %s" % ((m, l, n),))
