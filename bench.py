@@ -59,16 +59,21 @@ def code_sha(paths):
 
 # int8 warp-level tensor rate (mma.sync m16n8k32 .s8, dense) measured on a GB300
 # with register-resident operands: the peak for the int8 base case.
-S8_MMA_SYNC_TOPS = 150.3
+S8_MMA_SYNC_TOPS = 157.9
 # binary warp-level tensor rate (mma.sync m16n8k256 .b1 .and.popc: AND + popcount
 # per bit pair), measured the same way: the peak for the binary base case.
-B1_MMA_SYNC_TOPS = 146.2
+B1_MMA_SYNC_TOPS = 154.2
 # shared-memory read bandwidth of all 152 SMs measured on a GB300 at 2070 MHz by a
 # probe with the M4RM lookup pattern (each quarter-warp reads one 128-byte row as
-# 8 x 16 bytes, four independent rows in flight per thread): 121.5 B/clk/SM, 95 %
-# of the nominal 128 B/clk (152 x 128 B x 2070 MHz = 40.3 TB/s).  The peak for
-# the packed M4RM base cases.
-SMEM_LOOKUP_GBS = 38200.0
+# 8 x 16 bytes, four independent rows in flight per thread, one 256-thread CTA per
+# SM): 126.1 B/clk/SM, 98.5 % of the nominal 128 B/clk (152 x 128 B x 2070 MHz =
+# 40.3 TB/s).  The peak for the packed M4RM base cases (profiles/peaks.md).
+SMEM_LOOKUP_GBS = 39690.0
+# dense throughput of one tcgen05.mma.cta_group::1 stream per SM (M = 128, N = 256,
+# both operands in shared memory, 4 instructions per 128-byte K block) measured on a
+# GB300 at 2070 MHz: kind::f8f6f4 (E4M3) and kind::mxf4 (E2M1, scale factors in
+# tensor memory).  Context for the tensor-core rooflines (profiles/peaks.md).
+MMA_ONLY_TFLOPS = {"tc_fp8": 4855.9, "tc_fp4": 9710.9}
 
 
 def smem_peak(peaks):
@@ -103,12 +108,14 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--p", type=float, default=0.5, help="density of one bits (square workload)")
-    ap.add_argument("--paths", default="m4rm,tc_fp8,tc_s8,tc_b1", help="base cases to time")
+    ap.add_argument("--paths", default="m4rm,tc_fp4,tc_fp8,tc_s8,tc_b1", help="base cases to time")
     ap.add_argument("--depth", type=int, default=-1)
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--t", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (config 1, 2, 3 at n=65536, 4, 5) after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of one CPU-oracle sample")
     ap.add_argument("--workload", choices=["square", "batched", "chain", "sweep"], default="square",
@@ -227,13 +234,18 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
     """Roofline of the dominant kernel from its algorithmic work per launch."""
     if ms_per_launch <= 0:
         return None
-    if fam == "tc_fp8":
+    if fam in ("tc_fp8", "tc_fp4"):
         flops = 2.0 * M * L * N * leaves                    # dense 0/1 product, exact sums
         achieved = flops / (ms_per_launch * 1e-3) / 1e12
-        peak = 2.0 * peaks["bf16_tflops"]                    # FP8 = 2 x BF16 (nominal ratio)
+        ratio = 2.0 if fam == "tc_fp8" else 6.0              # nominal 4.5 / 13.5 vs 2.25 PFLOP/s bf16
+        peak = ratio * peaks["bf16_tflops"]
+        mma_only = MMA_ONLY_TFLOPS[fam]
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_note": "2 x bf16 burst of %s peaks (nominal fp8/bf16 ratio)" % peak_kind}
+                "frac": achieved / peak, "frac_of_mma_only": achieved / mma_only,
+                "traffic": ncu_traffic(fam, leaves, M, L, N),
+                "peak_note": "%g x bf16 burst of %s peaks (nominal %s/bf16 ratio); an MMA-only loop of "
+                             "this instruction on this GPU reaches %.0f TFLOP/s" % (
+                                 ratio, peak_kind, fam[3:], mma_only)}
     if fam == "tc_b1":
         ops = 2.0 * M * L * N * leaves                      # AND + popcount per bit pair, int32 sums
         achieved = ops / (ms_per_launch * 1e-3) / 1e12
@@ -253,8 +265,10 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
     smem_bytes = M * L * N / (8.0 * k) * leaves
     achieved = smem_bytes / (ms_per_launch * 1e-3) / 1e9
     peak, note = smem_peak(peaks)
+    nominal = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) / 1e3
     return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": ncu_traffic("m4rm", leaves, M, L, N),
+            "frac": achieved / peak, "frac_of_nominal": achieved / nominal,
+            "traffic": ncu_traffic("m4rm", leaves, M, L, N),
             "traffic_note": "DRAM bytes per launch, scaled by leaf operand bytes from a 49-leaf ncu capture",
             "peak_note": note}
 
@@ -284,6 +298,120 @@ def strassen_stream_bytes(M, L, N, d):
     return split, comb
 
 
+L2_BYTES = 129 * 2**20
+
+
+class L2Flush:
+    """Writes a buffer larger than the 129 MB L2 on the timing stream, so that
+    the next timed product starts from a cold cache."""
+
+    def __init__(self, torch):
+        self.buf = torch.empty(256 * 2**20, dtype=torch.uint8, device="cuda")
+        self.k = 0
+
+    def __call__(self):
+        self.k = (self.k + 1) & 0xFF
+        self.buf.fill_(self.k)
+
+
+def measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak_kind, local_rank,
+                    dist=None, rank=0, flush=None):
+    """One product configuration through gf2_mul: a first call (the autotuner's
+    choice for automatic options), `warmup` untimed calls, then `steps` calls
+    timed with CUDA events on the current stream, with the library's per-kernel
+    device-time accounting on, nvidia-smi clock samples around the timed region
+    and Freivalds' check of the result.  With `flush`, L2 is flushed before
+    every timed call and only the calls themselves are timed."""
+    stream = torch.cuda.current_stream()
+    g.gf2_mul(MC, MA, MB, o)
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as cs:
+        for _ in range(warmup):
+            g.gf2_mul(MC, MA, MB, o)
+        torch.cuda.synchronize()
+        plan = g.gf2_describe_plan(m, l, n, o)
+        if dist is not None:
+            dist.barrier()
+        launches0 = g.gf2_launch_count()
+        g.gf2_profile_enable(True)
+        torch.cuda.synchronize()
+        t_start = time.time()
+        if flush is None:
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(steps):
+                g.gf2_mul(MC, MA, MB, o)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_total = ev0.elapsed_time(ev1)
+        else:
+            pairs = []
+            for _ in range(steps):
+                flush()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.gf2_mul(MC, MA, MB, o)
+                e1.record(stream)
+                pairs.append((e0, e1))
+            torch.cuda.synchronize()
+            ms_total = sum(a.elapsed_time(b) for a, b in pairs)
+        t_end = time.time()
+    launches = g.gf2_launch_count() - launches0
+    fam = {}
+    for i, name in enumerate(g.PROFILE_FAMILIES):
+        t, c = g.gf2_profile_read(i)
+        if c:
+            fam[name] = {"ms": t, "launches": c}
+    g.gf2_profile_enable(False)
+    ms, _, value = aggregate(ms_total / steps, 2.0 * m * l * n)
+    bad = g.gf2_freivalds(MC, MA, MB, 1000 + rank)
+    kv = dict(x.split("=", 1) for x in plan.split() if "=" in x)
+    d = int(kv["depth"])
+    M, L, N = (int(x) for x in kv["leaf"].split("x"))
+    leaves = int(kv["leaves"])
+    k = int(kv.get("m4rm_k", 8))
+    dom = max(fam.items(), key=lambda kvp: kvp[1]["ms"])[0] if fam else None
+    dom_ms = fam[dom]["ms"] / max(fam[dom]["launches"], 1) if fam else 0.0
+    rl = roofline_for(dom, leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
+        if dom in BASE_FAMILIES else None
+    hbm = {}
+    Mp, Lp, Np = (int(x) for x in kv["padded"].split("x"))
+    sb, cb = strassen_stream_bytes(Mp, Lp, Np, d)
+    eb = expand_bytes(kv.get("base"), leaves, M, L, N)
+    for fam_name, nbytes in (("sw_split", sb), ("sw_combine", cb), ("expand", eb)):
+        if fam_name in fam and nbytes > 0:
+            per_step_ms = fam[fam_name]["ms"] / steps
+            gbs = nbytes / (per_step_ms * 1e-3) / 1e9
+            hbm[fam_name] = {"bound": "hbm", "bytes_per_step": nbytes, "ms_per_step": per_step_ms,
+                             "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": gbs / peaks["hbm_gbs"]}
+    return {
+        "ms": ms, "value": value, "depth": d, "plan": plan, "hbm_kernels": hbm,
+        "gpu_launches": launches, "kernels": fam, "dominant": dom,
+        "dominant_ms_per_launch": dom_ms, "roofline": rl, "steps": steps, "warmup": warmup,
+        "l2": "flushed (256 MiB written) before every timed call" if flush is not None else
+              "inputs and output exceed the 129 MB L2",
+        "freivalds_mismatched_rows": bad, "clocks": cs.summary(t_start, t_end),
+    }
+
+
+BASE_FAMILIES = ("m4rm", "tc_fp8", "tc_fp4", "tc_s8", "tc_b1")
+
+
+def expand_bytes(base, leaves, M, L, N):
+    """Algorithmic HBM bytes of the expansion of the leaf operands for the
+    tcgen05 base cases: the packed A and B^T leaves read once (M x L and
+    N x L bits), the expanded rows written once (L rounded up to 128 FP8 or
+    256 FP4 entries, one byte or half a byte per entry)."""
+    if base not in ("tc_fp8", "tc_fp4"):
+        return 0.0
+    epr, eb = (128, 1.0) if base == "tc_fp8" else (256, 0.5)
+    kp = -(-L // epr) * epr
+    return leaves * ((M + N) * L / 8.0 + (M + N) * kp * eb)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_0811_1714_gb300 as g
@@ -295,7 +423,6 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    stream = torch.cuda.current_stream()
 
     A = g.empty(m, l)
     B = g.empty(l, n)
@@ -307,78 +434,23 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_kind = load_peaks()
 
     avail = [p.strip() for p in args.paths.split(",") if p.strip()]
-    base_of = {"m4rm": g.GF2_BASE_M4RM, "tc_fp8": g.GF2_BASE_TC_FP8, "tc_s8": g.GF2_BASE_TC_S8,
-               "tc_b1": g.GF2_BASE_TC_B1}
     results = {}
     for path in avail:
-        o = g.opts(base=base_of[path], depth=args.depth, k=args.k if path == "m4rm" else 0,
+        o = g.opts(base=BASE_OF[path](g), depth=args.depth, k=args.k if path == "m4rm" else 0,
                    t=args.t if path == "m4rm" else 0)
         try:
-            g.gf2_mul(MC, MA, MB, o)        # first call: the autotuner picks the depth
+            results[path] = measure_product(g, torch, MC, MA, MB, m, l, n, o, args.steps, args.warmup,
+                                            peaks, peak_kind, local_rank, dist, rank)
         except g.GF2Error as e:
             results[path] = {"unavailable": str(e)}
-            continue
-        torch.cuda.synchronize()
-        with ClockSampler(local_rank) as cs:
-            for _ in range(args.warmup):
-                g.gf2_mul(MC, MA, MB, o)
-            torch.cuda.synchronize()
-            plan = g.gf2_describe_plan(m, l, n, o)
-            if dist is not None:
-                dist.barrier()
-            launches0 = g.gf2_launch_count()
-            g.gf2_profile_enable(True)
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            t_start = time.time()
-            ev0.record(stream)
-            for _ in range(args.steps):
-                g.gf2_mul(MC, MA, MB, o)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            t_end = time.time()
-        ms_total = ev0.elapsed_time(ev1)
-        launches = g.gf2_launch_count() - launches0
-        fam = {}
-        for i, name in enumerate(g.PROFILE_FAMILIES):
-            t, c = g.gf2_profile_read(i)
-            if c:
-                fam[name] = {"ms": t, "launches": c}
-        g.gf2_profile_enable(False)
-        ms, _, value = aggregate(ms_total / args.steps, 2.0 * m * l * n)
-        bad = g.gf2_freivalds(MC, MA, MB, 1000 + rank)
-        # plan fields
-        kv = dict(x.split("=", 1) for x in plan.split() if "=" in x)
-        d = int(kv["depth"])
-        M, L, N = (int(x) for x in kv["leaf"].split("x"))
-        leaves = int(kv["leaves"])
-        k = int(kv.get("m4rm_k", 8))
-        dom = max(fam.items(), key=lambda kvp: kvp[1]["ms"])[0] if fam else path
-        dom_ms = fam[dom]["ms"] / max(fam[dom]["launches"], 1) if fam else 0.0
-        rl = roofline_for(dom, leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
-            if dom in ("m4rm", "tc_fp8", "tc_s8", "tc_b1") else None
-        hbm = {}
-        Mp, Lp, Np = (int(x) for x in kv["padded"].split("x"))
-        sb, cb = strassen_stream_bytes(Mp, Lp, Np, d)
-        for fam_name, nbytes in (("sw_split", sb), ("sw_combine", cb)):
-            if fam_name in fam and nbytes > 0:
-                per_step_ms = fam[fam_name]["ms"] / args.steps
-                gbs = nbytes / (per_step_ms * 1e-3) / 1e9
-                hbm[fam_name] = {"bound": "hbm", "bytes_per_step": nbytes, "ms_per_step": per_step_ms,
-                                 "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                                 "frac": gbs / peaks["hbm_gbs"]}
-        results[path] = {
-            "ms": ms, "value": value, "depth": d, "plan": plan, "hbm_kernels": hbm,
-            "gpu_launches": launches, "kernels": fam, "dominant": dom,
-            "dominant_ms_per_launch": dom_ms, "roofline": rl,
-            "freivalds_mismatched_rows": bad, "clocks": cs.summary(t_start, t_end),
-        }
     ok = {p: r for p, r in results.items() if "ms" in r}
     if not ok:
         raise SystemExit("no base case ran: %s" % results)
     head = min(ok, key=lambda p: ok[p]["ms"])
     H = ok[head]
+    # leave C holding the headline path's product for the e2e comparison
+    g.gf2_mul(MC, MA, MB, g.opts(base=BASE_OF[head](g), depth=args.depth))
+    torch.cuda.synchronize()
 
     e2e = None
     if not args.no_e2e:
@@ -387,7 +459,7 @@ def run_ours(args, rank, world, local_rank):
         hA = A.cpu().pin_memory()
         hB = B.cpu().pin_memory()
         hC = torch.zeros_like(C, device="cpu").pin_memory()
-        o = g.opts(base=base_of[head], depth=args.depth)
+        o = g.opts(base=BASE_OF[head](g), depth=args.depth)
         hMA, hMB, hMC = g.mat(hA, l), g.mat(hB, n), g.mat(hC, n)
         for _ in range(max(1, args.warmup)):
             g.gf2_mul(hMC, hMA, hMB, o)
@@ -403,12 +475,15 @@ def run_ours(args, rank, world, local_rank):
                "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": (hA.numel() + hB.numel()) * 8,
                "d2h_bytes_per_step": hC.numel() * 8, "matches_device_result": same}
+        del hA, hB, hC
+    del A, B, C
+    torch.cuda.empty_cache()
 
     line = {
         "metric": METRIC, "value": H["value"], "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": H["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64-packed-bits" if head == "m4rm" else "fp8e4m3-0/1",
+        "dtype": DTYPE_OF[head],
         "data": "synthetic: SplitMix64 Bernoulli(%g) bits, seeds 1/2 (+100*rank)" % args.p,
         "config": {"workload": "square C=A*B over GF(2), m=l=n=%d" % n, "m": m, "l": l, "n": n, "p": args.p,
                    "base": head, "depth": H["depth"], "plan": H["plan"],
@@ -422,6 +497,78 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": None,
     }
     return line
+
+
+BASE_OF = {"m4rm": lambda g: g.GF2_BASE_M4RM, "tc_fp8": lambda g: g.GF2_BASE_TC_FP8,
+           "tc_fp4": lambda g: g.GF2_BASE_TC_FP4,
+           "tc_s8": lambda g: g.GF2_BASE_TC_S8, "tc_b1": lambda g: g.GF2_BASE_TC_B1,
+           "auto": lambda g: g.GF2_BASE_AUTO}
+DTYPE_OF = {"m4rm": "u64-packed-bits", "tc_fp8": "fp8e4m3-0/1", "tc_fp4": "fp4e2m1-0/1",
+            "tc_s8": "s8-0/1", "tc_b1": "b1-packed-bits"}
+
+
+def config_list(args):
+    """The other configurations of the workload, measured after the headline
+    by the default run: (name, m, l, n, p, path, options)."""
+    return [
+        ("config1_n1024_k8_depth0", 1024, 1024, 1024, 0.5, "m4rm", dict(depth=0, k=8)),
+        ("config2_n16384", 16384, 16384, 16384, 0.5, "auto", dict()),
+        ("config2_rect_20000x12000x28000", 20000, 12000, 28000, 0.5, "auto", dict()),
+        ("config3_n65536_p0.5_m4rm", 65536, 65536, 65536, 0.5, "m4rm", dict()),
+        ("config3_n65536_p0.9_m4rm", 65536, 65536, 65536, 0.9, "m4rm", dict()),
+        ("config3_n65536_p0.5_tc_fp8", 65536, 65536, 65536, 0.5, "tc_fp8", dict()),
+        ("config3_n65536_p0.9_tc_fp8", 65536, 65536, 65536, 0.9, "tc_fp8", dict()),
+        ("config3_n65536_p0.5_tc_fp4", 65536, 65536, 65536, 0.5, "tc_fp4", dict()),
+        ("config3_n65536_p0.9_tc_fp4", 65536, 65536, 65536, 0.9, "tc_fp4", dict()),
+    ]
+
+
+def run_configs(args, rank, world, local_rank):
+    """Every configuration besides the headline: config 1, config 2's other
+    shapes, config 3 at n = 65536 (p = 0.5 and 0.9, both base cases), the
+    4096-product batch (config 4) and the chain (config 5).  Fewer steps than
+    the headline (at most 10, at least 3 warm-up calls) keep the whole run
+    within a few minutes."""
+    import torch
+    import paper_0811_1714_gb300 as g
+
+    peaks, peak_kind = load_peaks()
+    steps = max(3, min(args.steps, 10))
+    warmup = max(3, min(args.warmup, 3))
+    flush = L2Flush(torch)
+    out = {}
+    for name, m, l, n, p, path, kw in config_list(args):
+        t0 = time.time()
+        A, B, C = g.empty(m, l), g.empty(l, n), g.empty(m, n)
+        MA, MB, MC = g.mat(A, l), g.mat(B, n), g.mat(C, n)
+        g.gf2_random(MA, 1 + 100 * rank, p)
+        g.gf2_random(MB, 2 + 100 * rank, p)
+        o = g.opts(base=BASE_OF[path](g), **kw)
+        small = (m * l + l * n) / 8 < 2 * L2_BYTES
+        try:
+            r = measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak_kind, local_rank,
+                                None, rank, flush if small else None)
+            r.update({"m": m, "l": l, "n": n, "p": p, "path": path, "wall_s": time.time() - t0})
+        except g.GF2Error as e:
+            r = {"unavailable": str(e)}
+        out[name] = r
+        del A, B, C, MA, MB, MC
+        torch.cuda.empty_cache()
+    del flush
+    torch.cuda.empty_cache()
+    t0 = time.time()
+    bargs = argparse.Namespace(**vars(args))
+    bargs.steps, bargs.warmup = steps, warmup
+    out["config4_batched_4096"] = run_batched(bargs, rank, 1, local_rank)
+    out["config4_batched_4096"]["wall_s"] = time.time() - t0
+    torch.cuda.empty_cache()
+    t0 = time.time()
+    cargs = argparse.Namespace(**vars(args))
+    cargs.steps, cargs.warmup = max(3, min(args.steps, 5)), warmup
+    out["config5_chain"] = run_chain(cargs, rank, 1, local_rank)
+    out["config5_chain"]["wall_s"] = time.time() - t0
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -505,24 +652,31 @@ def run_batched(args, rank, world, local_rank):
     variant = g.gf2_mul_batched_ex(arrs)          # first call: autotune + graph build
     stream = torch.cuda.current_stream()
 
-    def timed(options):
-        for _ in range(args.warmup):
-            g.gf2_mul_batched(arrs, options=options)
-        launches0 = g.gf2_launch_count()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            g.gf2_mul_batched(arrs, options=options)
-        ev1.record(stream)
-        torch.cuda.synchronize()
+    clocks = {}
+
+    def timed(options, tag):
+        g.gf2_mul_batched(arrs, options=options)      # first call for these options: tuning, graph
+        with ClockSampler(local_rank) as cs:
+            for _ in range(args.warmup):
+                g.gf2_mul_batched(arrs, options=options)
+            launches0 = g.gf2_launch_count()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                g.gf2_mul_batched(arrs, options=options)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t1 = time.time()
+        clocks[tag] = cs.summary(t0, t1)
         return ev0.elapsed_time(ev1) / args.steps, g.gf2_launch_count() - launches0
 
     def sampled_bad(seed0):
         return sum(1 for i in range(0, len(dims), 64) if g.gf2_freivalds(MC[i], MA[i], MB[i], seed0 + i))
 
     g.gf2_profile_enable(True)
-    ms_local, launches = timed(None)
+    ms_local, launches = timed(None, "m4rm")
     k_ms, k_n = g.gf2_profile_read(g.PROFILE_FAMILIES.index("batched"))
     g.gf2_profile_enable(False)
     bad = sampled_bad(5)
@@ -544,8 +698,8 @@ def run_batched(args, rank, world, local_rank):
     # the same batch on the tensor-core base case: one batched transpose and
     # one persistent tensor-core launch per step
     g.gf2_profile_enable(True)
-    tc_ms_local, tc_launches = timed(g.opts(base=g.GF2_BASE_TC_FP8, depth=0))
-    t_ms, t_n = g.gf2_profile_read(g.PROFILE_FAMILIES.index("tc_fp8"))
+    tc_ms_local, tc_launches = timed(g.opts(base=g.GF2_BASE_TC_FP8, depth=0), "tc_fp8")
+    t_ms, t_n = g.gf2_profile_read(g.PROFILE_FAMILIES.index("tc_fp8_packed"))
     g.gf2_profile_enable(False)
     tc_ms, _, tc_value = aggregate(tc_ms_local, ops)
     tc_rl = None
@@ -556,6 +710,7 @@ def run_batched(args, rank, world, local_rank):
         tc_rl = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                  "traffic": None, "peak_note": "2 x bf16 burst of %s peaks (nominal fp8/bf16 ratio)" % peak_kind}
     tc = {"ms_per_step": tc_ms, "value": tc_value, "gpu_launches": tc_launches, "roofline": tc_rl,
+          "clocks": clocks.get("tc_fp8"),
           "graph": "batched transpose of every B + one persistent tensor-core kernel",
           "freivalds_sampled_products_failed": sampled_bad(9)}
     ops = ops_all
@@ -566,7 +721,8 @@ def run_batched(args, rank, world, local_rank):
         "dtype": "u64-packed-bits", "data": "synthetic: SplitMix64 bits, dims log-uniform [64, 2048] seed 42",
         "config": {"workload": "4096 batched products, m,l,n log-uniform in [64, 2048]",
                    "variant": g.gf2_batched_variant_name(variant), "total_bit_ops": ops},
-        "gpu_launches": launches, "roofline": rl,
+        "gpu_launches": launches, "roofline": rl, "clocks": clocks.get("m4rm"),
+        "l2": "operands of all products (about 0.5 GB) exceed the 129 MB L2",
         "graph": "each step replays one CUDA graph: counter reset + one persistent kernel",
         "verified": {"freivalds_sampled_products_failed": bad},
         "tc_fp8_base": tc,
@@ -587,23 +743,35 @@ def run_chain(args, rank, world, local_rank):
     g.gf2_random(MA, 31 + 100 * rank)
     g.gf2_random(MB, 32 + 100 * rank)
     g.gf2_random(MC, 33 + 100 * rank)
-    plans = [g.gf2_describe_plan(M, K1, N1), g.gf2_describe_plan(M, N1, N2)]
     for _ in range(max(1, args.warmup)):
         g.gf2_mul(MAB, MA, MB)
         g.gf2_mul(MABC, MAB, MC)
+    plans = [g.gf2_describe_plan(M, K1, N1), g.gf2_describe_plan(M, N1, N2)]
     stream = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     torch.cuda.synchronize()
     t1 = t2 = 0.0
-    for _ in range(args.steps):
-        ev[0].record(stream)
-        g.gf2_mul(MAB, MA, MB)
-        ev[1].record(stream)
-        g.gf2_mul(MABC, MAB, MC)
-        ev[2].record(stream)
-        torch.cuda.synchronize()
-        t1 += ev[0].elapsed_time(ev[1])
-        t2 += ev[1].elapsed_time(ev[2])
+    launches0 = g.gf2_launch_count()
+    g.gf2_profile_enable(True)
+    with ClockSampler(local_rank) as cs:
+        ts0 = time.time()
+        for _ in range(args.steps):
+            ev[0].record(stream)
+            g.gf2_mul(MAB, MA, MB)
+            ev[1].record(stream)
+            g.gf2_mul(MABC, MAB, MC)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            t1 += ev[0].elapsed_time(ev[1])
+            t2 += ev[1].elapsed_time(ev[2])
+        ts1 = time.time()
+    launches = g.gf2_launch_count() - launches0
+    fam = {}
+    for i, name in enumerate(g.PROFILE_FAMILIES):
+        t, c = g.gf2_profile_read(i)
+        if c:
+            fam[name] = {"ms_per_step": t / args.steps, "launches_per_step": c / args.steps}
+    g.gf2_profile_enable(False)
     t1 /= args.steps
     t2 /= args.steps
     ops1, ops2 = 2.0 * M * K1 * N1, 2.0 * M * N1 * N2
@@ -615,7 +783,9 @@ def run_chain(args, rank, world, local_rank):
         "ms_per_step": t1 + t2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "auto", "data": "synthetic: SplitMix64 Bernoulli(1/2) bits, seeds 31/32/33",
         "config": {"workload": "chain 131072x65536 . 65536x131072 . 131072x8192", "plans": plans,
-                   "stage_ms": [t1, t2]},
+                   "stage_ms": [t1, t2],
+                   "l2": "operands (1 GiB and more each) exceed the 129 MB L2"},
+        "gpu_launches": launches, "kernels": fam, "clocks": cs.summary(ts0, ts1),
         "verified": {"freivalds_both_stages": ok},
     }
 
@@ -692,6 +862,8 @@ def main():
             print(json.dumps(line), flush=True)
         return
     line = run_ours(args, rank, world, local_rank)
+    if world == 1 and not args.no_configs:
+        line["configs"] = run_configs(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds)

@@ -62,13 +62,17 @@ extern "C" {
 /* ---- base cases -------------------------------------------------------- */
 #define GF2_BASE_AUTO   0      /* autotuner's choice                                         */
 #define GF2_BASE_M4RM   1      /* Method of the Four Russians on packed words (Sections 3.x) */
-#define GF2_BASE_TC_FP8 2      /* 0/1 FP8 e4m3 tensor-core product, parity of exact sums    */
+#define GF2_BASE_TC_FP8 2      /* 0/1 FP8 e4m3 tensor-core product, parity of exact sums
+                                  (Section 2.3); operands expanded once to FP8 bytes        */
 #define GF2_BASE_TC_S8  3      /* 0/1 int8 warp-level tensor product (mma.sync), int32 sums;
                                   never chosen automatically (slow on this part)             */
 #define GF2_BASE_TC_B1  4      /* binary warp-level tensor product on the packed words
                                   (mma.sync .b1 .and.popc, Section 2.3's popcount of
                                   AND-ed rows of A and B^T), int32 sums; never chosen
                                   automatically (slow on this part)                          */
+#define GF2_BASE_TC_FP4 5      /* 0/1 FP4 e2m1 block-scaled tensor-core product (scale
+                                  factors 1.0), parity of exact sums (Section 2.3);
+                                  operands expanded once to FP4 nibbles                     */
 
 typedef struct gf2_mat {
     uint64_t *data;        /* first word of row 0                                  */
@@ -297,11 +301,14 @@ int gf2_profile_enable(int32_t on);
 /* gf2_profile_read waits for the recorded events and returns the summed
  * device time (ms) and launch count of one kernel family (Section 6's
  * timings split by step):
- *   0 m4rm base case (Section 3), 1 tensor-core base case (Section 2.3),
+ *   0 m4rm base case (Section 3), 1 FP8 tensor-core base case (Section 2.3),
  *   2 Strassen split, 3 Strassen combine (Section 4, Algorithm 4),
  *   4 transpose, 5 generator, 6 Freivalds products, 7 MakeTable
  *   (Algorithm 1), 8 batched base case, 9 int8 tensor-core base case,
- *   10 binary tensor-core base case (Section 2.3).
+ *   10 binary tensor-core base case, 11 FP4 tensor-core base case,
+ *   12 expansion of packed operands to FP8 / FP4 entries, 13 FP8 tensor-core
+ *   kernel of the batched form (packed operands expanded on chip)
+ *   (Section 2.3).
  */
 int gf2_profile_read(int32_t family, double *ms, int64_t *launches);
 

@@ -22,9 +22,10 @@ Entry points keep the C names of every symbol in ``include/gf2.h`` (listed in
 failure detection (``gf2_device_status``, ``gf2_selftest_wait``).
 
 Base cases (``opts(base=...)``): ``GF2_BASE_AUTO`` (the autotuner's choice),
-``GF2_BASE_M4RM`` (packed Method of the Four Russians), ``GF2_BASE_TC_FP8``
-(exact 0/1 FP8 tcgen05 products), and the warp-level ``GF2_BASE_TC_S8``
-(int8) and ``GF2_BASE_TC_B1`` (1-bit AND + popcount) forms.
+``GF2_BASE_M4RM`` (packed Method of the Four Russians), ``GF2_BASE_TC_FP8`` and
+``GF2_BASE_TC_FP4`` (exact 0/1 FP8 / block-scaled FP4 tcgen05 products on
+operands expanded once in HBM), and the warp-level ``GF2_BASE_TC_S8`` (int8)
+and ``GF2_BASE_TC_B1`` (1-bit AND + popcount) forms.
 """
 from __future__ import annotations
 
@@ -54,6 +55,7 @@ GF2_BASE_M4RM = 1
 GF2_BASE_TC_FP8 = 2
 GF2_BASE_TC_S8 = 3
 GF2_BASE_TC_B1 = 4
+GF2_BASE_TC_FP4 = 5
 
 #: every symbol declared in include/gf2.h
 EXPORTS = (
@@ -379,7 +381,8 @@ def gf2_profile_name(family: int):
 
 
 PROFILE_FAMILIES = ("m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose", "random",
-                    "freivalds", "make_table", "batched", "tc_s8", "tc_b1")
+                    "freivalds", "make_table", "batched", "tc_s8", "tc_b1", "tc_fp4", "expand",
+                    "tc_fp8_packed")
 
 
 # ---- torch conveniences ----------------------------------------------------

@@ -30,8 +30,13 @@ namespace {
 // The tensor-core base cases read B transposed (rows of B^T = columns of B).
 bool is_tc(int base)
 {
-    return base == GF2_BASE_TC_FP8 || base == GF2_BASE_TC_S8 || base == GF2_BASE_TC_B1;
+    return base == GF2_BASE_TC_FP8 || base == GF2_BASE_TC_S8 || base == GF2_BASE_TC_B1 || base == GF2_BASE_TC_FP4;
 }
+
+// The tcgen05 base cases run on operands expanded once in HBM (FP8 bytes or
+// FP4 nibbles); the warp-level ones read the packed words.
+bool is_expanded(int base) { return base == GF2_BASE_TC_FP8 || base == GF2_BASE_TC_FP4; }
+int kind_of(int base) { return base == GF2_BASE_TC_FP4 ? KIND_F4 : KIND_F8; }
 
 const char *base_name(int base)
 {
@@ -39,6 +44,7 @@ const char *base_name(int base)
     case GF2_BASE_TC_FP8: return "tc_fp8";
     case GF2_BASE_TC_S8: return "tc_s8";
     case GF2_BASE_TC_B1: return "tc_b1";
+    case GF2_BASE_TC_FP4: return "tc_fp4";
     default: return "m4rm";
     }
 }
@@ -153,7 +159,7 @@ gf2_opts resolve(const gf2_opts *o)
 
 int check_opts(const gf2_opts &o)
 {
-    if (o.base < GF2_BASE_AUTO || o.base > GF2_BASE_TC_B1) return GF2_EINVAL;
+    if (o.base < GF2_BASE_AUTO || o.base > GF2_BASE_TC_FP4) return GF2_EINVAL;
     if (o.depth < -1 || o.depth > 8) return GF2_EINVAL;
     if (o.k < 0 || o.k > 10 || o.t < 0 || o.t > 16) return GF2_EINVAL;
     if (o.accumulate != 0 && o.accumulate != 1) return GF2_EINVAL;
@@ -185,6 +191,8 @@ struct Plan {
     int64_t slabA[kMaxDepth + 1], slabB[kMaxDepth + 1], slabP[kMaxDepth + 1];
     size_t offBt;        // transposed B (tensor-core base, depth 0 or top of the split;
     int64_t ldBt;        // the cubic form: 64 rows)
+    size_t offXA, offXB; // expanded leaf operands (FP8 / FP4 tensor-core base cases)
+    int64_t rowbytes;    // bytes per expanded row
     bool cubic;          // depth 0, at most 64 columns: the cubic product of Section 2.3
     size_t bytes;        // total device scratch (without host staging)
 };
@@ -211,7 +219,7 @@ int make_plan(int64_t m, int64_t l, int64_t n, const gf2_opts &o, Plan *p)
     p->m = m; p->l = l; p->n = n;
     p->base = o.base;
     if (p->base == GF2_BASE_AUTO) p->base = GF2_BASE_M4RM;
-    if (p->base == GF2_BASE_TC_FP8 && !tc_fp8_available()) return GF2_EUNSUPPORTED;
+    if (is_expanded(p->base) && !tc_fp8_available()) return GF2_EUNSUPPORTED;
     p->depth = (o.depth < 0) ? auto_depth(m, l, n, p->base) : o.depth;
     if (m == 0 || n == 0 || l == 0) p->depth = 0;
     const int d = p->depth;
@@ -251,6 +259,14 @@ int make_plan(int64_t m, int64_t l, int64_t n, const gf2_opts &o, Plan *p)
         p->ldBt = even_up(words_of(l));
         p->offBt = take((size_t)(n * p->ldBt) * 8);
     }
+    if (is_expanded(p->base) && m > 0 && l > 0 && n > 0) {
+        // every leaf operand expanded once: A leaves (Md rows) and B^T leaves
+        // (Nd rows), rows of rowbytes
+        const int64_t Md = d ? (p->M >> d) : m, Ld = d ? (p->L >> d) : l, Nd = d ? (p->N >> d) : n;
+        p->rowbytes = tc_expanded_rowbytes(kind_of(p->base), Ld);
+        p->offXA = take((size_t)(cnt * Md) * (size_t)p->rowbytes);
+        p->offXB = take((size_t)(cnt * Nd) * (size_t)p->rowbytes);
+    }
     // a right factor of at most 64 columns (Section 2.3, the paper's choice
     // over M4RM there): one word of C per row, from B's columns as rows
     p->cubic = (p->base == GF2_BASE_M4RM && d == 0 && o.k == 0 && o.t == 0 && m > 0 && l > 0 && n > 0 &&
@@ -278,8 +294,24 @@ std::string plan_text(const Plan &p)
 // Base case over `batch` products with dense or user layouts.
 int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const uint64_t *B,
              int64_t ldb, int64_t bsB, uint64_t *C, int64_t ldc, int64_t bsC, int64_t m, int64_t l,
-             int64_t n, int batch, int accumulate, cudaStream_t s)
+             int64_t n, int batch, int accumulate, char *scratch, cudaStream_t s)
 {
+    if (is_expanded(p.base)) {
+        // expand the packed leaves once (HBM-bound), then the MMA kernel
+        const int kind = kind_of(p.base);
+        uint8_t *XA = reinterpret_cast<uint8_t *>(scratch + p.offXA);
+        uint8_t *XB = reinterpret_cast<uint8_t *>(scratch + p.offXB);
+        int rc = tc_expand_launch(kind, A, lda, bsA, m, l, batch, XA, p.rowbytes, s);
+        if (!rc) rc = tc_expand_launch(kind, B, ldb, bsB, n, l, batch, XB, p.rowbytes, s);
+        if (rc) return rc;
+        TcxLaunch X;
+        X.kind = kind;
+        X.XA = XA; X.XB = XB; X.rowbytes = p.rowbytes;
+        X.C = C; X.ldc = ldc; X.bsC = bsC;
+        X.m = m; X.n = n; X.batch = batch; X.accumulate = accumulate;
+        if ((rc = tc_status_address(&X.status))) return rc;
+        return tc_mma_launch(X, s);
+    }
     if (is_tc(p.base)) {
         TcLaunch L;
         L.A = A; L.lda = lda; L.bsA = bsA;
@@ -344,10 +376,8 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         }
     }
     if (b_ready) GF2_CUDA_TRY(cudaStreamWaitEvent(s, b_ready, 0));
-    // the FP8 base case reads B^T with each 32-bit half bit-reversed (its
-    // expansion order); the transpose writes it so, with the tail beyond l
-    // already cleared
-    const bool rev32 = (p.base == GF2_BASE_TC_FP8);
+    // every tensor-core base case of gf2_mul reads B^T in natural bit order
+    const bool rev32 = false;
     if (tc) {
         uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
         DMat T{Bt, n, l, p.ldBt};
@@ -369,7 +399,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     }
     if (d == 0)
         return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
-                        m, l, n, 1, accumulate, s);
+                        m, l, n, 1, accumulate, scratch, s);
 
     // top-down: the additions of Algorithm 4 (the left factor's above, the
     // right factor's here) for every sub-problem of each level; two levels
@@ -418,7 +448,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         int rc = run_base(p, reinterpret_cast<const uint64_t *>(scratch + p.offA[d]), p.ldA[d], p.slabA[d],
                           reinterpret_cast<const uint64_t *>(scratch + p.offB[d]), p.ldB[d], p.slabB[d],
                           reinterpret_cast<uint64_t *>(scratch + p.offP[d]), p.ldP[d], p.slabP[d], Md, Ld,
-                          Nd, (int)cnt, 0, s);
+                          Nd, (int)cnt, 0, scratch, s);
         if (rc) return rc;
     }
     // bottom-up: the 7 final additions of Algorithm 4, Augment and Stack,
@@ -543,6 +573,8 @@ std::string tune_key(int64_t m, int64_t l, int64_t n, const gf2_opts &o)
     return b;
 }
 
+constexpr size_t kTuneScratchCap = (size_t)48 << 30;   // bytes of scratch a timed candidate may need
+
 // The plan(s) to run: one resolved option set, or the candidates to time.
 bool wants_tuning(int64_t m, int64_t l, int64_t n, const gf2_opts &o, std::vector<gf2_opts> *cands,
                   std::string *key)
@@ -568,7 +600,10 @@ bool wants_tuning(int64_t m, int64_t l, int64_t n, const gf2_opts &o, std::vecto
     if (o.base != GF2_BASE_AUTO) bases.push_back(o.base);
     else {
         bases.push_back(GF2_BASE_M4RM);
-        if (tc_fp8_available()) bases.push_back(GF2_BASE_TC_FP8);
+        if (tc_fp8_available()) {
+            bases.push_back(GF2_BASE_TC_FP4);
+            bases.push_back(GF2_BASE_TC_FP8);
+        }
     }
     for (int base : bases) {
         std::vector<int> depths;
@@ -585,9 +620,14 @@ bool wants_tuning(int64_t m, int64_t l, int64_t n, const gf2_opts &o, std::vecto
             gf2_opts r = o;
             r.base = base;
             r.depth = d;
+            // skip plans whose scratch alone would take a large share of the
+            // device (expanded tensor-core operands deep in the recursion)
+            Plan pl;
+            if (make_plan(m, l, n, r, &pl) != GF2_OK || pl.bytes > kTuneScratchCap) continue;
             cands->push_back(r);
         }
     }
+    if (cands->empty()) cands->push_back(o);
     if (cands->size() <= 1) return false;
     return true;
 }
@@ -858,7 +898,8 @@ int gf2_profile_read(int32_t family, double *ms, int64_t *launches)
 const char *gf2_profile_name(int32_t family)
 {
     static const char *names[PF_COUNT] = {"m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose",
-                                          "random", "freivalds", "make_table", "batched", "tc_s8", "tc_b1"};
+                                          "random", "freivalds", "make_table", "batched", "tc_s8", "tc_b1",
+                                          "tc_fp4", "expand", "tc_fp8_packed"};
     if (family < 0 || family >= PF_COUNT) return nullptr;
     return names[family];
 }

@@ -40,7 +40,7 @@ void note_launch(int n = 1);
 
 // Kernel families for the device-time accounting of gf2_profile_*.
 enum ProfFamily { PF_M4RM = 0, PF_TC, PF_SPLIT, PF_COMBINE, PF_TRANSPOSE, PF_RANDOM, PF_MATVEC,
-                  PF_TABLE, PF_BATCHED, PF_TC_S8, PF_TC_B1, PF_COUNT };
+                  PF_TABLE, PF_BATCHED, PF_TC_S8, PF_TC_B1, PF_TC_F4, PF_EXPAND, PF_TC_PACKED, PF_COUNT };
 
 // Brackets the launches made during its lifetime with CUDA events on `s`
 // when accounting is on.
@@ -132,6 +132,32 @@ struct TcLaunch {
     unsigned int *status;                    // device word for timeouts (may be null)
 };
 int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
+// Device status word of the tensor-core kernels' bounded waits.
+int tc_status_address(unsigned int **p);
+
+// Tensor-core base case on operands expanded once in HBM (tc_mma.cu):
+// KIND_F8 = FP8 E4M3 0/1 bytes (kind::f8f6f4), KIND_F4 = FP4 E2M1 0/1
+// nibbles (kind::mxf4, scale factors 1.0).  Each operand row of l entries
+// becomes tc_expanded_rowbytes(kind, l) bytes (l rounded up to 128 FP8 or
+// 256 FP4 entries, zeros beyond l).
+enum TcKind { KIND_F8 = 0, KIND_F4 = 1 };
+int64_t tc_expanded_rowbytes(int kind, int64_t l);
+// Y (batch x rows rows of rowbytes bytes) = expansion of the packed X
+// (batch x rows x cols, stride ld words, batch stride bs words).
+int tc_expand_launch(int kind, const uint64_t *X, int64_t ld, int64_t bs, int64_t rows, int64_t cols, int batch,
+                     uint8_t *Y, int64_t rowbytes, cudaStream_t s);
+struct TcxLaunch {
+    int kind;
+    const uint8_t *XA;       // batch x m expanded rows of A
+    const uint8_t *XB;       // batch x n expanded rows of B^T
+    int64_t rowbytes;        // bytes per expanded row (a multiple of 128)
+    uint64_t *C; int64_t ldc, bsC;   // m x n packed
+    int64_t m, n;
+    int batch;
+    int accumulate;
+    unsigned int *status;
+};
+int tc_mma_launch(const TcxLaunch &L, cudaStream_t s);
 int tc_s8_launch(const TcLaunch &L, cudaStream_t s);
 // Binary tensor-core base case (mma.sync .b1 .and.popc on the packed words).
 int tc_b1_launch(const TcLaunch &L, cudaStream_t s);

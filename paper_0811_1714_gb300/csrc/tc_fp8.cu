@@ -781,6 +781,12 @@ int wait_selftest_launch(long long limit, cudaStream_t s)
     return check_launch();
 }
 
+int tc_status_address(unsigned int **p)
+{
+    GF2_CUDA_TRY(cudaGetSymbolAddress((void **)p, g_tc_status));
+    return GF2_OK;
+}
+
 int tc_status_read_and_clear(unsigned int *out, cudaStream_t s)
 {
     unsigned int *p = nullptr;
@@ -828,7 +834,7 @@ int tc_fp8_launch(const TcLaunch &L, cudaStream_t s)
     GF2_CUDA_TRY(cudaGetDevice(&dev));
     GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t grid = P.tiles < sms ? P.tiles : sms;
-    ProfScope ps(PF_TC, s);
+    ProfScope ps(PF_TC_PACKED, s);
     tc_fp8_kernel<<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(mapA, mapB, P);
     note_launch();
     return check_launch();
@@ -875,7 +881,7 @@ int tc_batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *
     for (auto it = g_tcb.begin(); it != g_tcb.end(); ++it) {
         if (it->key == key) {
             g_tcb.splice(g_tcb.begin(), g_tcb, it);
-            ProfScope ps(PF_TC, s);
+            ProfScope ps(PF_TC_PACKED, s);
             GF2_CUDA_TRY(cudaGraphLaunch(g_tcb.front().exec, s));
             note_launch(2);
             return GF2_OK;
@@ -982,7 +988,7 @@ int tc_batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *
     }
     if (cudaGraphInstantiate(&e.exec, e.graph, 0) != cudaSuccess) { cudaGetLastError(); tcb_free(e); return GF2_ECUDA; }
     {
-        ProfScope ps(PF_TC, s);
+        ProfScope ps(PF_TC_PACKED, s);
         if (cudaGraphLaunch(e.exec, s) != cudaSuccess) { tcb_free(e); return GF2_ECUDA; }
     }
     note_launch(2);

@@ -1,0 +1,482 @@
+// tc_mma.cu -- exact tensor-core base case on operands expanded once in HBM:
+// C = A B over GF(2) from 0/1 products on the 5th-generation tensor cores
+// (tcgen05, sm_103a), in two number formats:
+//   KIND_F8: FP8 E4M3, a 1-bit is the byte 0x38 (1.0), kind::f8f6f4;
+//   KIND_F4: FP4 E2M1, a 1-bit is the nibble 0x2 (1.0), two entries per
+//            byte, kind::mxf4 with block scale factors that are all 1.0
+//            (UE8M0 127), so every block product is the plain product.
+//
+// Why it is exact (Section 2.3): a GF(2) dot product is an AND followed by an
+// XOR accumulation, i.e. the parity of the INTEGER dot product of the 0/1
+// vectors.  Each product of two entries is 0 or 1.0, and a K-chunk of at most
+// KCHUNK = 4096 entries sums to an integer count <= 2^12, which any
+// accumulator keeping 13 or more significant bits holds exactly (FP32 keeps
+// 24).  After each chunk the accumulator D is read from tensor memory; the
+// parity of count is the last mantissa bit of D + 2^23 (whose ulp is 1), and
+// the parities of successive chunks are XORed: the GF(2) sum over all of K.
+//
+// Two kernels:
+//  - expand_kernel<KIND>: the packed operand rows (Section 2.1 layout, a
+//    batch of equal matrices) become rows of FP8 bytes or FP4 nibbles, padded
+//    with zeros to a whole number of 128-byte rows of K (128 FP8 or 256 FP4
+//    entries).  HBM-bound: it reads each packed word once and writes 8 (FP8)
+//    or 4 (FP4) times its bytes.
+//  - tc_mma_kernel<KIND>: persistent, one CTA per SM, 128 x 256 tiles of C.
+//    Warp 0 issues TMA tensor copies of 128-byte K blocks of the expanded A
+//    (128 rows) and B^T (256 rows) into a 4-stage ring in the 128-byte
+//    swizzled K-major layout the MMA reads; warp 1 owns the tensor memory and
+//    one of its threads issues tcgen05.mma.cta_group::1 (M = 128, N = 256,
+//    K = 32 FP8 / 64 FP4 entries per instruction, four per stage, A and B
+//    both from shared memory) into FP32 accumulators in tensor memory (two
+//    of 256 columns for FP8; one for FP4, whose scale factors fill columns
+//    256-287 and 320-351); warps 2-9 (two per tensor-memory lane quarter, one
+//    per 128-column half) read an accumulator with tcgen05.ld, hand it back
+//    at once, and turn the 128 FP32 values of a thread into parity words of C
+//    in registers.  No bit expansion competes with the tensor core.
+// Hand-offs use mbarriers: full (TMA transaction bytes) / empty (one
+// tcgen05.commit per stage) per stage, accumulator full (commit) / empty
+// (eight epilogue arrivals).  Every wait is bounded: an expired wait records
+// GF2_ETIMEOUT in the device status word and the CTA winds down (waits for its
+// copies and MMAs in flight, frees its tensor memory) instead of hanging.
+#include "common.cuh"
+#include "tcgen05.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+namespace gf2 {
+namespace {
+
+using namespace gf2::tc;
+
+constexpr int BM = 128;                       // tile rows (MMA M)
+constexpr int BN = 256;                       // tile columns (MMA N)
+constexpr int ROWB = 128;                     // bytes of K per operand row per stage
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * ROWB;            // 16 KB
+constexpr int B_BYTES = BN * ROWB;            // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int KCHUNK = 4096;                  // exact-sum bound (entries per accumulation)
+constexpr int TMA_WARP = 0, MMA_WARP = 1, EPI_WARP0 = 2, NUM_EPI_WARPS = 8;
+constexpr int NTHREADS = (EPI_WARP0 + NUM_EPI_WARPS) * 32;    // 320
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t SFA_COL = 256, SFB_COL = 320;  // FP4 scale factors (32 columns each)
+constexpr int NBARS = 2 * STAGES + 4 + 1;
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + NBARS * 8 + 16;
+static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+
+template <int KIND> struct Fmt;
+template <> struct Fmt<KIND_F8> {
+    static constexpr int EPR = 128;           // entries per 128-byte row
+    static constexpr int NACC = 2;            // accumulators in tensor memory
+    // D = F32 (bits 4-5 = 1), A = B = E4M3 (bits 7-9, 10-12 = 0), both
+    // K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+template <> struct Fmt<KIND_F4> {
+    static constexpr int EPR = 256;
+    static constexpr int NACC = 1;
+    // block-scaled descriptor: scale-factor ids 0 (bits 4-5, 29-30), A = B =
+    // E2M1 (code 1 at bits 7-9 and 10-12), both K-major, N >> 3 at bits
+    // 17-22, scale type UE8M0 (bit 23 = 1), M >> 4 at bits 24-28
+    static constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
+struct Params {
+    int64_t m, n;            // rows of A (and of C), rows of B^T (columns of C) per product
+    int64_t nkb;             // 128-byte K blocks per row
+    int tiles_m, tiles_n;
+    int64_t tiles;           // batch * tiles_m * tiles_n
+    uint64_t *C;
+    int64_t ldc, bsC;
+    int accumulate;
+    unsigned int *status;
+};
+
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t ad, uint64_t bd, uint32_t tmem_base, uint32_t acc)
+{
+    if (KIND == KIND_F8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+            ::"r"(d), "l"(ad), "l"(bd), "r"(Fmt<KIND_F8>::IDESC), "r"(acc)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
+            ::"r"(d), "l"(ad), "l"(bd), "r"(Fmt<KIND_F4>::IDESC), "r"(tmem_base + SFA_COL),
+              "r"(tmem_base + SFB_COL), "r"(acc)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, int &tm, int &tn)
+{
+    const int64_t per = (int64_t)P.tiles_m * P.tiles_n;
+    b = (int)(t / per);
+    const int64_t r = t - (int64_t)b * per;
+    tm = (int)(r / P.tiles_n);
+    tn = (int)(r - (int64_t)tm * P.tiles_n);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Params P)
+{
+    constexpr int NACC = Fmt<KIND>::NACC;
+    constexpr int KB_PER_CHUNK = KCHUNK / Fmt<KIND>::EPR;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // stages sit on 1024-byte boundaries (128-byte swizzle atoms)
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *sbase = smem_raw + (base - raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sbase + STAGES * STAGE_BYTES);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NBARS);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto tempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    const uint32_t done_bar = bar0 + 8u * (2 * STAGES + 4);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);            // the TMA thread's expect_tx arrival
+            mbar_init(empty_bar(s), 1);           // tcgen05.commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull_bar(b), 1);
+            mbar_init(tempty_bar(b), NUM_EPI_WARPS);
+        }
+        mbar_init(done_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == MMA_WARP) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    if (KIND == KIND_F4 && warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
+        // every scale factor 1.0 (UE8M0 127): whatever bytes of these columns
+        // the MMA reads for A and for B, each block product is unscaled
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+        tmem_fill32(tmem_base + lanes + SFA_COL, 0x7F7F7F7Fu);
+        tmem_fill32(tmem_base + lanes + SFB_COL, 0x7F7F7F7Fu);
+        tmem_wait_st();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+
+    // every role walks the CTA's tiles t = blockIdx.x, +gridDim.x, ...
+    if (warp == TMA_WARP) {
+        // ------------------------------------------------------------ TMA issuer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mapA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
+            int64_t q = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+                int b, tm, tn;
+                tile_coords(P, t, b, tm, tn);
+                for (int64_t kb = 0; kb < P.nkb; ++kb, ++q) {
+                    const int s = (int)(q % STAGES);
+                    if (!mbar_wait(empty_bar(s), (uint32_t)((q / STAGES) & 1) ^ 1u, P.status, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t dst = base + s * STAGE_BYTES;
+                    mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
+                    tma_load_3d(dst, &mapA, (int)(kb * ROWB), tm * BM, b, full_bar(s));
+                    tma_load_3d(dst + A_BYTES, &mapB, (int)(kb * ROWB), tn * BN, b, full_bar(s));
+                }
+            }
+            // wind down: copies issued but not consumed (only after an abort)
+            // still land in shared memory; wait for them before the CTA exits
+            for (int64_t r = (q > STAGES ? q - STAGES : 0); r < q; ++r)
+                mbar_drain(full_bar((int)(r % STAGES)), (uint32_t)((r / STAGES) & 1), P.status);
+        }
+        __syncwarp();
+    } else if (warp == MMA_WARP) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, u = 0;                      // stages, accumulator uses
+            bool ok = true;
+            const int nchunks = (int)((P.nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
+            for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+                for (int c = 0; c < nchunks && ok; ++c, ++u) {
+                    const int ab = (int)(u % NACC);
+                    if (!mbar_wait(tempty_bar(ab), ((u / NACC) & 1u) ^ 1u, P.status, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t dt = tmem_base + (uint32_t)ab * 256u;
+                    const int64_t kb0 = (int64_t)c * KB_PER_CHUNK;
+                    const int64_t kb1 = std::min<int64_t>(P.nkb, kb0 + KB_PER_CHUNK);
+                    for (int64_t kb = kb0; kb < kb1; ++kb, ++it) {
+                        const int s = (int)(it % STAGES);
+                        if (!mbar_wait(full_bar(s), (it / STAGES) & 1u, P.status, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)     // 32 bytes of K per instruction
+                            mma_issue<KIND>(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
+                                            tmem_base, (kb > kb0 || kk > 0) ? 1u : 0u);
+                        mma_commit(empty_bar(s));           // stage free once these MMAs have read it
+                    }
+                    if (!ok) break;
+                    mma_commit(tfull_bar(ab));              // accumulator ready for the epilogue
+                }
+            }
+            // wind down: wait until every issued MMA has completed
+            mma_commit(done_bar);
+            mbar_drain(done_bar, 0, P.status);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;                   // TMEM lanes 32*quarter.. = tile rows
+        const int half = (warp - EPI_WARP0) >> 2;       // columns 128*half ..
+        const int row_in_tile = quarter * 32 + lane;
+        const int nchunks = (int)((P.nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
+        const int64_t nW = words_of(P.n);
+        uint32_t u = 0;
+        for (int64_t t = blockIdx.x; t < P.tiles && !warp_aborted(abort_flag); t += gridDim.x) {
+            int b, tm, tn;
+            tile_coords(P, t, b, tm, tn);
+            uint32_t par[4] = {0u, 0u, 0u, 0u};
+            bool ok = true;
+            for (int c = 0; c < nchunks; ++c, ++u) {
+                const int ab = (int)(u % NACC);
+                if (!warp_wait(tfull_bar(ab), (u / NACC) & 1u, P.status, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t taddr =
+                    tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)ab * 256u + (uint32_t)half * 128u;
+                uint32_t r[128];
+                tmem_ld32(taddr, r);
+                tmem_ld32(taddr + 32, r + 32);
+                tmem_ld32(taddr + 64, r + 64);
+                tmem_ld32(taddr + 96, r + 96);
+                tmem_wait_ld();
+                // the accumulator is in registers: hand it back to the MMA
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty_bar(ab));
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        // D = count <= 2^12, an integer: the ulp of D + 2^23 is 1
+                        const uint32_t f = __float_as_uint(__uint_as_float(r[32 * g + j]) + 8388608.0f);
+                        word |= (f & 1u) << j;
+                    }
+                    par[g] ^= word;
+                }
+            }
+            if (!ok) break;
+            const int64_t grow = (int64_t)tm * BM + row_in_tile;
+            if (grow < P.m) {
+                uint64_t *C = P.C + (int64_t)b * P.bsC + grow * P.ldc;
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const int64_t wcol = (int64_t)tn * (BN / 64) + half * 2 + i;
+                    if (wcol < nW) {
+                        const uint64_t v = (((uint64_t)par[2 * i + 1] << 32) | par[2 * i]) & word_mask(wcol, P.n);
+                        C[wcol] = P.accumulate ? (C[wcol] ^ v) : v;
+                    }
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == MMA_WARP) tmem_dealloc(tmem_base, TMEM_COLS);
+}
+
+// 4 bits -> 4 bytes of 0x00 / 0x38 (E4M3 1.0): the multiply places bit i of
+// the nibble at bit 8i (the four shifted copies do not overlap), the mask
+// keeps those bits, the second multiply turns each into 0x38.
+__device__ __forceinline__ uint32_t f8_of_nibble(uint32_t v)
+{
+    return ((v * 0x00204081u) & 0x01010101u) * 0x38u;
+}
+
+// 8 bits -> 8 nibbles of 0x0 / 0x2 (E2M1 1.0), bit i in nibble i: spread by
+// halves, quarters and eighths, then shift each bit to nibble bit 1.
+__device__ __forceinline__ uint32_t f4_of_byte(uint32_t v)
+{
+    v &= 0xFFu;
+    v = (v | (v << 12)) & 0x000F000Fu;
+    v = (v | (v << 6)) & 0x03030303u;
+    v = (v | (v << 3)) & 0x11111111u;
+    return v << 1;
+}
+
+// Rows of a batch of packed matrices (rows x cols, stride ld, batch stride
+// bs words) -> rows of `rowbytes` expanded bytes (entries beyond cols 0),
+// row f = b * rows + r at Y + f * rowbytes.  One warp per row at a time.
+template <int KIND>
+__global__ void __launch_bounds__(256)
+expand_kernel(const uint64_t *__restrict__ X, int64_t ld, int64_t bs, int64_t rows, int64_t cols, int64_t nrows,
+              uint8_t *__restrict__ Y, int64_t rowbytes)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t W = words_of(cols);
+    const int64_t kpw = rowbytes / (KIND == KIND_F8 ? 64 : 32);      // packed words per expanded row
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < nrows; f += nwarps) {
+        const int64_t b = f / rows, r = f - b * rows;
+        const uint64_t *src = X + b * bs + r * ld;
+        uint8_t *dst = Y + f * rowbytes;
+        for (int64_t w = lane; w < kpw; w += 32) {
+            const uint64_t x = (w < W) ? (src[w] & word_mask(w, cols)) : 0ull;
+            if (KIND == KIND_F8) {
+                uint4 *o = reinterpret_cast<uint4 *>(dst + w * 64);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t h = (uint32_t)(x >> (16 * q));
+                    o[q] = make_uint4(f8_of_nibble(h & 15u), f8_of_nibble((h >> 4) & 15u),
+                                      f8_of_nibble((h >> 8) & 15u), f8_of_nibble((h >> 12) & 15u));
+                }
+            } else {
+                uint4 *o = reinterpret_cast<uint4 *>(dst + w * 32);
+                const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+                o[0] = make_uint4(f4_of_byte(lo), f4_of_byte(lo >> 8), f4_of_byte(lo >> 16), f4_of_byte(lo >> 24));
+                o[1] = make_uint4(f4_of_byte(hi), f4_of_byte(hi >> 8), f4_of_byte(hi >> 16), f4_of_byte(hi >> 24));
+            }
+        }
+    }
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once.
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn()
+{
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(p);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D byte map over expanded rows: x = byte in the row (rowbytes), y = row
+// (rows; rows beyond arrive as zeros), z = product of the batch.  Box: one
+// 128-byte K block x box_rows, 128-byte swizzle.
+int make_map(CUtensorMap *map, const uint8_t *base, int64_t rowbytes, int64_t rows, int batch, int box_rows)
+{
+    EncodeFn fn = encode_fn();
+    if (!fn) return GF2_EUNSUPPORTED;
+    const cuuint64_t dims[3] = {(cuuint64_t)rowbytes, (cuuint64_t)rows, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)rowbytes, (cuuint64_t)(rows * rowbytes)};
+    const cuuint32_t box[3] = {(cuuint32_t)ROWB, (cuuint32_t)box_rows, 1u};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? GF2_OK : GF2_ECUDA;
+}
+
+template <int KIND>
+int mma_launch(const TcxLaunch &L, cudaStream_t s)
+{
+    Params P;
+    P.m = L.m; P.n = L.n;
+    P.nkb = L.rowbytes / ROWB;
+    P.tiles_m = div_up(L.m, BM);
+    P.tiles_n = div_up(L.n, BN);
+    P.tiles = (int64_t)L.batch * P.tiles_m * P.tiles_n;
+    P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
+    P.accumulate = L.accumulate;
+    P.status = L.status;
+    CUtensorMap mapA, mapB;
+    int rc = make_map(&mapA, L.XA, L.rowbytes, L.m, L.batch, BM);
+    if (rc) return rc;
+    rc = make_map(&mapB, L.XB, L.rowbytes, L.n, L.batch, BN);
+    if (rc) return rc;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(tc_mma_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    });
+    if (attr_err != cudaSuccess) return GF2_ECUDA;
+    int dev = 0, sms = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t grid = P.tiles < sms ? P.tiles : sms;
+    ProfScope ps(KIND == KIND_F8 ? PF_TC : PF_TC_F4, s);
+    tc_mma_kernel<KIND><<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(mapA, mapB, P);
+    note_launch();
+    return check_launch();
+}
+
+}  // namespace
+
+int64_t tc_expanded_rowbytes(int kind, int64_t l)
+{
+    const int64_t epr = kind == KIND_F8 ? 128 : 256;
+    const int64_t kp = (l + epr - 1) / epr * epr;
+    return kind == KIND_F8 ? kp : kp / 2;
+}
+
+int tc_expand_launch(int kind, const uint64_t *X, int64_t ld, int64_t bs, int64_t rows, int64_t cols, int batch,
+                     uint8_t *Y, int64_t rowbytes, cudaStream_t s)
+{
+    const int64_t nrows = (int64_t)batch * rows;
+    if (nrows <= 0 || rowbytes <= 0) return GF2_OK;
+    if ((reinterpret_cast<uintptr_t>(Y) & 15) || (rowbytes % ROWB)) return GF2_ELAYOUT;
+    int dev = 0, sms = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t want = (nrows + 7) / 8;                  // 8 warps per block, one row each
+    const int64_t grid = std::min<int64_t>(want, (int64_t)sms * 16);
+    ProfScope ps(PF_EXPAND, s);
+    if (kind == KIND_F8)
+        expand_kernel<KIND_F8><<<(unsigned)grid, 256, 0, s>>>(X, ld, bs, rows, cols, nrows, Y, rowbytes);
+    else
+        expand_kernel<KIND_F4><<<(unsigned)grid, 256, 0, s>>>(X, ld, bs, rows, cols, nrows, Y, rowbytes);
+    note_launch();
+    return check_launch();
+}
+
+int tc_mma_launch(const TcxLaunch &L, cudaStream_t s)
+{
+    if (L.batch <= 0 || L.m <= 0 || L.n <= 0) return GF2_OK;
+    if ((reinterpret_cast<uintptr_t>(L.XA) & 15) || (reinterpret_cast<uintptr_t>(L.XB) & 15) ||
+        (L.rowbytes % ROWB) || L.rowbytes <= 0)
+        return GF2_ELAYOUT;
+    if (L.m > INT32_MAX || L.n > INT32_MAX || L.rowbytes > INT32_MAX || L.batch > 65535) return GF2_EUNSUPPORTED;
+    return L.kind == KIND_F8 ? mma_launch<KIND_F8>(L, s) : mma_launch<KIND_F4>(L, s);
+}
+
+}  // namespace gf2

@@ -56,15 +56,16 @@ PEAKS = {"hbm_gbs": 6780.7, "bf16_tflops": 1896.1, "sm_max_mhz": 2070.0}
 def test_m4rm_roofline_counts_table_row_reads():
     """n = 32768 at depth 4: 2401 leaves of 2048^3, k = 8, so one launch
     reads 2401 * 2048^3 / 64 = 3.22e11 table bytes; at 11.47 ms that is
-    28.1 TB/s of the 38.2 TB/s measured with the lookup pattern (the nominal
+    28.1 TB/s of the 39.69 TB/s measured with the lookup pattern (the nominal
     152 x 128 B x 2070 MHz is 40.27 TB/s)."""
     r = bench.roofline_for("m4rm", 2401, 2048, 2048, 2048, 8, 11.47, PEAKS, "measured")
     assert r["bound"] == "smem" and r["unit"] == "GB/s"
     assert 2401 * 2048 ** 3 / 64 == pytest.approx(3.2226e11, rel=1e-4)
-    assert r["peak"] == pytest.approx(38200.0)
+    assert r["peak"] == pytest.approx(39690.0)
     assert "40.3 TB/s" in r["peak_note"]
     assert r["achieved"] == pytest.approx(3.2226e11 / 11.47e-3 / 1e9, rel=1e-4)
-    assert round(r["frac"], 3) == 0.735
+    assert round(r["frac"], 3) == 0.708
+    assert round(r["frac_of_nominal"], 3) == 0.698
 
 
 def test_tc_roofline_counts_dense_flops_against_twice_bf16():
@@ -75,6 +76,21 @@ def test_tc_roofline_counts_dense_flops_against_twice_bf16():
     assert r["peak"] == pytest.approx(3792.2)
     assert r["achieved"] == pytest.approx(2.0 * 4096 ** 3 * 343 / 21.5e-3 / 1e12)
     assert round(r["frac"], 2) == 0.58
+
+
+def test_fp4_roofline_is_six_times_bf16():
+    """FP4 against 6 x the measured bf16 rate (nominal 13.5 vs 2.25 PFLOP/s)."""
+    r = bench.roofline_for("tc_fp4", 49, 8192, 8192, 8192, 0, 10.0, PEAKS, "measured")
+    assert r["peak"] == pytest.approx(6 * 1896.1)
+    assert r["achieved"] == pytest.approx(2.0 * 8192 ** 3 * 49 / 10.0e-3 / 1e12)
+
+
+def test_expansion_bytes():
+    """FP8: one byte per entry (K rounded up to 128); FP4: half a byte (K
+    rounded up to 256); plus the packed leaves read once."""
+    assert bench.expand_bytes("tc_fp8", 1, 128, 100, 256) == pytest.approx((384 * 100) / 8 + 384 * 128)
+    assert bench.expand_bytes("tc_fp4", 2, 128, 300, 256) == pytest.approx(2 * ((384 * 300) / 8 + 384 * 512 * 0.5))
+    assert bench.expand_bytes("m4rm", 1, 128, 100, 256) == 0.0
 
 
 def test_code_sha_ignores_comments_but_not_code(tmp_path):

@@ -119,7 +119,7 @@ def test_argument_checks(lib):
     assert rc_of(g.gf2_mul, Cal, Aal, SQ) == g.GF2_EALIAS
     # bad options
     assert rc_of(g.gf2_mul, C, A, B, g.opts(base=7)) == g.GF2_EINVAL
-    assert rc_of(g.gf2_mul, C, A, B, g.opts(base=g.GF2_BASE_TC_B1 + 1)) == g.GF2_EINVAL
+    assert rc_of(g.gf2_mul, C, A, B, g.opts(base=g.GF2_BASE_TC_FP4 + 1)) == g.GF2_EINVAL
     assert rc_of(g.gf2_mul, C, A, B, g.opts(depth=-2)) == g.GF2_EINVAL
     assert rc_of(g.gf2_mul, C, A, B, g.opts(k=3, t=3)) == g.GF2_EUNSUPPORTED
     o = g.opts()

@@ -57,19 +57,20 @@ def check_product(m, l, n, base, p=0.5, seeds=(1, 2), blocks=4, depth=-1):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("base", [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_S8, g.GF2_BASE_TC_B1])
+@pytest.mark.parametrize("base", [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_FP4, g.GF2_BASE_TC_S8,
+                                  g.GF2_BASE_TC_B1])
 def test_square_32768(base):
     check_product(32768, 32768, 32768, base)
 
 
-@pytest.mark.parametrize("base", [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8])
+@pytest.mark.parametrize("base", [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_FP4])
 def test_rectangular_20000_12000_28000(base):
     """Widths 12000 and 28000 are not multiples of 64 (padding in every level)."""
     check_product(20000, 12000, 28000, base, seeds=(5, 6))
 
 
-@pytest.mark.parametrize("base,p", [(g.GF2_BASE_M4RM, 0.5), (g.GF2_BASE_TC_FP8, 0.5),
-                                    (g.GF2_BASE_M4RM, 0.9), (g.GF2_BASE_TC_FP8, 0.9)])
+@pytest.mark.parametrize("base,p", [(g.GF2_BASE_M4RM, 0.5), (g.GF2_BASE_TC_FP8, 0.5), (g.GF2_BASE_TC_FP4, 0.5),
+                                    (g.GF2_BASE_M4RM, 0.9), (g.GF2_BASE_TC_FP8, 0.9), (g.GF2_BASE_TC_FP4, 0.9)])
 def test_square_65536(base, p):
     check_product(65536, 65536, 65536, base, p=p, seeds=(11, 12), blocks=2)
 

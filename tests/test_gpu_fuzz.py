@@ -1,4 +1,4 @@
-"""Seeded random cases over every base case, Strassen-Winograd depths,
+"""Seeded random cases over every base case (50: ten per base case), Strassen-Winograd depths,
 accumulate mode and user strides, each bit-exact against the CPU oracle.
 
 Strides are padded beyond the logical width by random even amounts and the
@@ -45,8 +45,8 @@ def with_garbage(X, cols, extra, rng):
 
 CASES = []
 _r = np.random.default_rng(20260)
-for _i in range(40):
-    base = [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_S8, g.GF2_BASE_TC_B1][_i % 4]
+for _i in range(50):
+    base = [g.GF2_BASE_M4RM, g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_S8, g.GF2_BASE_TC_B1, g.GF2_BASE_TC_FP4][_i % 5]
     depth = int(_r.integers(0, 3))
     m, l, n = (int(x) for x in _r.integers(1, 2600, size=3))
     if depth:

@@ -1,8 +1,10 @@
-"""Parity of the tensor-core base case (0/1 FP8 products, parity of exact sums).
+"""Parity of the tcgen05 tensor-core base cases (0/1 FP8 and block-scaled FP4
+products on operands expanded once in HBM, parity of exact sums).
 
 Bit-exact against the CPU oracle.  The adversarial inputs for exactness are
-all-ones operands: every dot product then equals the K extent, the largest
-sum a chunk can hold, so a lost low bit anywhere would flip the parity.
+all-ones operands, whose dot products all equal the K extent, the largest
+sum a chunk can hold, and staircase right factors, whose dot products take
+every value up to K (so a lost low bit of any partial sum flips a parity).
 """
 import numpy as np
 import pytest
@@ -16,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_0811_1714_gb300 as g  # noqa: E402
 
-TC = g.GF2_BASE_TC_FP8
+TCS = [g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_FP4]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -29,64 +31,86 @@ def _lib():
     torch.cuda.synchronize()
 
 
-def tc_mul(A, B, m, l, n, depth=0, accumulate=0, C0=None):
+def tc_mul(A, B, m, l, n, depth=0, accumulate=0, C0=None, base=g.GF2_BASE_TC_FP8):
     Ad, Bd = to_dev(A), to_dev(B)
     C = to_dev(C0) if C0 is not None else g.empty(m, n)
-    g.gf2_mul(g.mat(C, n), g.mat(Ad, l), g.mat(Bd, n), g.opts(base=TC, depth=depth, accumulate=accumulate))
+    g.gf2_mul(g.mat(C, n), g.mat(Ad, l), g.mat(Bd, n), g.opts(base=base, depth=depth, accumulate=accumulate))
     g.gf2_device_status()
     return to_host(C)
 
 
+@pytest.mark.parametrize("base", TCS)
 @pytest.mark.parametrize("m,l,n", [
     (128, 128, 256), (1, 1, 1), (200, 300, 500), (128, 4096, 256), (130, 4097, 300),
-    (1024, 1000, 1100), (300, 9000, 700), (4096, 512, 4096)])
-def test_tc_base_case_parity(m, l, n):
+    (1024, 1000, 1100), (300, 9000, 700), (4096, 512, 4096), (129, 257, 257)])
+def test_tc_base_case_parity(m, l, n, base):
     A = synth.random_packed(m, l, synth.SEED_A)
     B = synth.random_packed(l, n, synth.SEED_B)
     ref = oracle.mul_packed(A, B, m, l, n)
-    assert_same_bits(tc_mul(A, B, m, l, n), ref, n, "tc %s" % ((m, l, n),))
+    assert_same_bits(tc_mul(A, B, m, l, n, base=base), ref, n, "tc %d %s" % (base, (m, l, n)))
 
 
+@pytest.mark.parametrize("base", TCS)
 @pytest.mark.parametrize("l", [4095, 4096, 4097, 8192, 12345])
-def test_tc_all_ones_at_the_chunk_bound(l):
+def test_tc_all_ones_at_the_chunk_bound(l, base):
     m, n = 256, 512
     A = synth.pack_bits(np.ones((m, l), np.uint8))
     B = synth.pack_bits(np.ones((l, n), np.uint8))
     expect = synth.pack_bits(np.full((m, n), l & 1, np.uint8))
-    assert_same_bits(tc_mul(A, B, m, l, n), expect, n, "ones l=%d" % l)
+    assert_same_bits(tc_mul(A, B, m, l, n, base=base), expect, n, "ones l=%d" % l)
 
 
-def test_tc_density_09():
+@pytest.mark.parametrize("base", TCS)
+@pytest.mark.parametrize("l", [4096, 6144, 9000])
+def test_tc_staircase_sums(l, base):
+    """A all ones, column j of B ones in rows 0..c_j - 1 with c_j running over
+    0..l: entry (i, j) of C is c_j mod 2.  Every count up to l occurs, so
+    every partial sum of a K-chunk has its low bits exercised."""
+    m, n = 130, 520
+    c = (np.arange(n) * 4099) % (l + 1)
+    c[:3] = [l, l - 1, 4095 if l > 4095 else 1]
+    Bb = (np.arange(l)[:, None] < c[None, :]).astype(np.uint8)
+    A = synth.pack_bits(np.ones((m, l), np.uint8))
+    B = synth.pack_bits(Bb)
+    expect = synth.pack_bits(np.repeat((c & 1)[None, :].astype(np.uint8), m, axis=0))
+    assert_same_bits(tc_mul(A, B, m, l, n, base=base), expect, n, "staircase l=%d" % l)
+
+
+@pytest.mark.parametrize("base", TCS)
+def test_tc_density_09(base):
     m, l, n = 640, 5000, 768
     A = synth.random_packed(m, l, 3, p=0.9)
     B = synth.random_packed(l, n, 4, p=0.9)
-    assert_same_bits(tc_mul(A, B, m, l, n), oracle.mul_packed(A, B, m, l, n), n, "p=0.9")
+    assert_same_bits(tc_mul(A, B, m, l, n, base=base), oracle.mul_packed(A, B, m, l, n), n, "p=0.9")
 
 
+@pytest.mark.parametrize("base", TCS)
 @pytest.mark.parametrize("m,l,n,depth", [(1024, 1024, 1024, 1), (1500, 2100, 1300, 2), (2048, 2048, 2048, 3)])
-def test_tc_under_strassen_winograd(m, l, n, depth):
+def test_tc_under_strassen_winograd(m, l, n, depth, base):
     A = synth.random_packed(m, l, synth.SEED_A)
     B = synth.random_packed(l, n, synth.SEED_B)
     ref = oracle.mul_packed(A, B, m, l, n)
-    assert_same_bits(tc_mul(A, B, m, l, n, depth=depth), ref, n, "tc depth %d" % depth)
+    assert_same_bits(tc_mul(A, B, m, l, n, depth=depth, base=base), ref, n, "tc depth %d" % depth)
 
 
-def test_tc_accumulate():
+@pytest.mark.parametrize("base", TCS)
+def test_tc_accumulate(base):
     m, l, n = 300, 700, 500
     A = synth.random_packed(m, l, 7)
     B = synth.random_packed(l, n, 8)
     C0 = synth.random_packed(m, n, 9)
     ref = oracle.mul_packed(A, B, m, l, n) ^ C0
-    assert_same_bits(tc_mul(A, B, m, l, n, accumulate=1, C0=C0), ref, n, "tc accumulate")
+    assert_same_bits(tc_mul(A, B, m, l, n, accumulate=1, C0=C0, base=base), ref, n, "tc accumulate")
 
 
-def test_tc_matches_m4rm_on_the_same_inputs():
+@pytest.mark.parametrize("base", TCS)
+def test_tc_matches_m4rm_on_the_same_inputs(base):
     m = l = n = 4096
     A = synth.random_packed(m, l, 21)
     B = synth.random_packed(l, n, 22)
     Ad, Bd = to_dev(A), to_dev(B)
     C1, C2 = g.empty(m, n), g.empty(m, n)
-    g.gf2_mul(g.mat(C1, n), g.mat(Ad, l), g.mat(Bd, n), g.opts(base=TC, depth=0))
+    g.gf2_mul(g.mat(C1, n), g.mat(Ad, l), g.mat(Bd, n), g.opts(base=base, depth=0))
     g.gf2_mul(g.mat(C2, n), g.mat(Ad, l), g.mat(Bd, n), g.opts(base=g.GF2_BASE_M4RM, depth=0))
     g.gf2_device_status()
     assert torch.equal(C1, C2)
