@@ -38,6 +38,11 @@ NCU_TRAFFIC = {
     "m4rm": {"sha": "1e46ef05f46c7c8d", "sources": ["paper_0811_1714_gb300/csrc/m4rm.cu",
                                                   "paper_0811_1714_gb300/csrc/m4rm_dev.cuh"],
              "bytes_per_operand_byte": 0.8845},
+    # profiles/tc_mma_kernel_fp4_n8192_depth1.md: 127.8 MB per launch against 117.4 MB of
+    # expanded leaf operands + 14.7 MB of packed leaf products
+    "tc_fp4": {"sha": "e845068149b4b7c6", "sources": ["paper_0811_1714_gb300/csrc/tc_mma.cu",
+                                        "paper_0811_1714_gb300/csrc/tcgen05.cuh"],
+               "bytes_per_operand_byte": 0.967},
 }
 
 
@@ -86,6 +91,18 @@ def smem_peak(peaks):
                   (peak / 1000.0, mhz, 152 * 128 * mhz / 1e6))
 
 
+def operand_bytes(fam, leaves, M, L, N):
+    """Bytes of the leaf operands a base-case launch reads and writes once:
+    packed A, B and C for M4RM; the expanded A and B^T rows (FP8 bytes or
+    FP4 nibbles, K rounded up to a 128-byte row) and packed C for the
+    tcgen05 forms."""
+    if fam in ("tc_fp8", "tc_fp4"):
+        epr, eb = (128, 1.0) if fam == "tc_fp8" else (256, 0.5)
+        kp = -(-L // epr) * epr
+        return leaves * ((M + N) * kp * eb + M * N / 8.0)
+    return leaves * (M * L + L * N + M * N) / 8.0
+
+
 def ncu_traffic(fam, leaves, M, L, N):
     """Per-launch DRAM bytes scaled from the capture, or None if the kernel changed."""
     ent = NCU_TRAFFIC.get(fam)
@@ -96,7 +113,7 @@ def ncu_traffic(fam, leaves, M, L, N):
             return None
     except OSError:
         return None
-    return ent["bytes_per_operand_byte"] * leaves * (M * L + L * N + M * N) / 8.0
+    return ent["bytes_per_operand_byte"] * operand_bytes(fam, leaves, M, L, N)
 UNIT = "bit-ops/s"
 
 
@@ -190,9 +207,11 @@ class ClockSampler:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
         return False
 
-    def summary(self, t0=None, t1=None):
+    def summary(self, t0=None, t1=None, pad=0.5):
         """Median SM clock, max clock and throttle reasons of the samples taken
-        between host times t0 and t1 (all samples when none fall inside)."""
+        between host times t0 and t1; when none fall inside (a timed region
+        shorter than the sampling period), the samples within `pad` seconds
+        of it; else all samples."""
         import datetime
         rows = []
         for ln in self.lines:
@@ -210,8 +229,12 @@ class ClockSampler:
         window = "timed region"
         if t0 is not None and t1 is not None:
             inside = [r for r in rows if r[0] is not None and t0 <= r[0] <= t1]
+            near = [r for r in rows if r[0] is not None and t0 - pad <= r[0] <= t1 + pad]
             if inside:
                 rows = inside
+            elif near:
+                rows = near
+                window = "within %.1f s of the timed region (shorter than the sampling period)" % pad
             else:
                 window = "whole run (no sample inside the timed region)"
         else:
@@ -314,8 +337,22 @@ class L2Flush:
         self.buf.fill_(self.k)
 
 
+class _Held:
+    """A running ClockSampler shared by several measurements (summaries are
+    taken after it stops)."""
+
+    def __init__(self, cs):
+        self.cs = cs
+
+    def __enter__(self):
+        return self.cs
+
+    def __exit__(self, *exc):
+        return False
+
+
 def measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak_kind, local_rank,
-                    dist=None, rank=0, flush=None):
+                    dist=None, rank=0, flush=None, sampler=None):
     """One product configuration through gf2_mul: a first call (the autotuner's
     choice for automatic options), `warmup` untimed calls, then `steps` calls
     timed with CUDA events on the current stream, with the library's per-kernel
@@ -325,7 +362,7 @@ def measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak
     stream = torch.cuda.current_stream()
     g.gf2_mul(MC, MA, MB, o)
     torch.cuda.synchronize()
-    with ClockSampler(local_rank) as cs:
+    with (ClockSampler(local_rank) if sampler is None else _Held(sampler)) as cs:
         for _ in range(warmup):
             g.gf2_mul(MC, MA, MB, o)
         torch.cuda.synchronize()
@@ -393,7 +430,8 @@ def measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak
         "dominant_ms_per_launch": dom_ms, "roofline": rl, "steps": steps, "warmup": warmup,
         "l2": "flushed (256 MiB written) before every timed call" if flush is not None else
               "inputs and output exceed the 129 MB L2",
-        "freivalds_mismatched_rows": bad, "clocks": cs.summary(t_start, t_end),
+        "freivalds_mismatched_rows": bad,
+        "clocks": cs.summary(t_start, t_end) if sampler is None else None, "timed_window": (t_start, t_end),
     }
 
 
@@ -438,9 +476,12 @@ def run_ours(args, rank, world, local_rank):
     for path in avail:
         o = g.opts(base=BASE_OF[path](g), depth=args.depth, k=args.k if path == "m4rm" else 0,
                    t=args.t if path == "m4rm" else 0)
+        small = (m * l + l * n) / 8 < 2 * L2_BYTES
         try:
             results[path] = measure_product(g, torch, MC, MA, MB, m, l, n, o, args.steps, args.warmup,
-                                            peaks, peak_kind, local_rank, dist, rank)
+                                            peaks, peak_kind, local_rank, dist, rank,
+                                            L2Flush(torch) if small else None)
+            results[path].pop("timed_window", None)
         except g.GF2Error as e:
             results[path] = {"unavailable": str(e)}
     ok = {p: r for p, r in results.items() if "ms" in r}
@@ -488,8 +529,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": "square C=A*B over GF(2), m=l=n=%d" % n, "m": m, "l": l, "n": n, "p": args.p,
                    "base": head, "depth": H["depth"], "plan": H["plan"],
                    "parallelism": "independent product per GPU" if world > 1 else "single GPU",
-                   "l2": "inputs 2 x %d MiB + output %d MiB exceed the 129 MB L2" % (
-                       m * l // 8 // 2**20, m * n // 8 // 2**20)},
+                   "l2": H["l2"]},
         "roofline": H["roofline"], "gpu_launches": H["gpu_launches"],
         "clocks": H["clocks"], "e2e": e2e,
         "verified": {"freivalds_64_vectors_mismatched_rows": H["freivalds_mismatched_rows"]},
@@ -537,6 +577,9 @@ def run_configs(args, rank, world, local_rank):
     warmup = max(3, min(args.warmup, 3))
     flush = L2Flush(torch)
     out = {}
+    cs = ClockSampler(local_rank)
+    cs.__enter__()
+    time.sleep(0.5)                      # nvidia-smi is sampling before the first timed region
     for name, m, l, n, p, path, kw in config_list(args):
         t0 = time.time()
         A, B, C = g.empty(m, l), g.empty(l, n), g.empty(m, n)
@@ -547,13 +590,18 @@ def run_configs(args, rank, world, local_rank):
         small = (m * l + l * n) / 8 < 2 * L2_BYTES
         try:
             r = measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak_kind, local_rank,
-                                None, rank, flush if small else None)
+                                None, rank, flush if small else None, sampler=cs)
             r.update({"m": m, "l": l, "n": n, "p": p, "path": path, "wall_s": time.time() - t0})
         except g.GF2Error as e:
             r = {"unavailable": str(e)}
         out[name] = r
         del A, B, C, MA, MB, MC
         torch.cuda.empty_cache()
+    time.sleep(0.3)
+    cs.__exit__(None, None, None)
+    for r in out.values():
+        if "timed_window" in r:
+            r["clocks"] = cs.summary(*r.pop("timed_window"))
     del flush
     torch.cuda.empty_cache()
     t0 = time.time()

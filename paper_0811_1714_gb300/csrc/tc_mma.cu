@@ -20,7 +20,7 @@
 //    batch of equal matrices) become rows of FP8 bytes or FP4 nibbles, padded
 //    with zeros to a whole number of 128-byte rows of K (128 FP8 or 256 FP4
 //    entries).  HBM-bound: it reads each packed word once and writes 8 (FP8)
-//    or 4 (FP4) times its bytes.
+//    or 4 (FP4) times its bytes, in coalesced 512-byte warp stores.
 //  - tc_mma_kernel<KIND>: persistent, one CTA per SM, 128 x 256 tiles of C.
 //    Warp 0 issues TMA tensor copies of 128-byte K blocks of the expanded A
 //    (128 rows) and B^T (256 rows) into a 4-stage ring in the 128-byte
@@ -88,7 +88,7 @@ struct Params {
     int64_t m, n;            // rows of A (and of C), rows of B^T (columns of C) per product
     int64_t nkb;             // 128-byte K blocks per row
     int tiles_m, tiles_n;
-    int64_t tiles;           // batch * tiles_m * tiles_n
+    int batch;
     uint64_t *C;
     int64_t ldc, bsC;
     int accumulate;
@@ -116,6 +116,7 @@ __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t ad, uint64_t bd, 
     }
 }
 
+// Tile t -> (batch, tile row, tile column).
 __device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, int &tm, int &tn)
 {
     const int64_t per = (int64_t)P.tiles_m * P.tiles_n;
@@ -178,6 +179,7 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     fence_before();
     __syncthreads();
     fence_after();
+    const int64_t tiles = (int64_t)P.tiles_m * P.tiles_n * P.batch;
 
     // every role walks the CTA's tiles t = blockIdx.x, +gridDim.x, ...
     if (warp == TMA_WARP) {
@@ -187,7 +189,7 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
             int64_t q = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+            for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 int b, tm, tn;
                 tile_coords(P, t, b, tm, tn);
                 for (int64_t kb = 0; kb < P.nkb; ++kb, ++q) {
@@ -214,7 +216,7 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             uint32_t it = 0, u = 0;                      // stages, accumulator uses
             bool ok = true;
             const int nchunks = (int)((P.nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
-            for (int64_t t = blockIdx.x; t < P.tiles && ok; t += gridDim.x) {
+            for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
                 for (int c = 0; c < nchunks && ok; ++c, ++u) {
                     const int ab = (int)(u % NACC);
                     if (!mbar_wait(tempty_bar(ab), ((u / NACC) & 1u) ^ 1u, P.status, abort_flag)) {
@@ -256,7 +258,7 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         const int nchunks = (int)((P.nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
         const int64_t nW = words_of(P.n);
         uint32_t u = 0;
-        for (int64_t t = blockIdx.x; t < P.tiles && !warp_aborted(abort_flag); t += gridDim.x) {
+        for (int64_t t = blockIdx.x; t < tiles && !warp_aborted(abort_flag); t += gridDim.x) {
             int b, tm, tn;
             tile_coords(P, t, b, tm, tn);
             uint32_t par[4] = {0u, 0u, 0u, 0u};
@@ -335,36 +337,44 @@ __device__ __forceinline__ uint32_t f4_of_byte(uint32_t v)
 
 // Rows of a batch of packed matrices (rows x cols, stride ld, batch stride
 // bs words) -> rows of `rowbytes` expanded bytes (entries beyond cols 0),
-// row f = b * rows + r at Y + f * rowbytes.  One warp per row at a time.
+// row f = b * rows + r at Y + f * rowbytes.  A warp takes 32 consecutive
+// words of a row (one coalesced 256-byte load) and writes their expansion as
+// 16-byte chunks, chunk c of the group by lane c mod 32 (each store
+// instruction writes 512 contiguous bytes); the word a chunk comes from is
+// fetched from its lane by a shuffle.
 template <int KIND>
 __global__ void __launch_bounds__(256)
 expand_kernel(const uint64_t *__restrict__ X, int64_t ld, int64_t bs, int64_t rows, int64_t cols, int64_t nrows,
               uint8_t *__restrict__ Y, int64_t rowbytes)
 {
+    constexpr int CPW = KIND == KIND_F8 ? 4 : 2;                     // 16-byte chunks per packed word
     const int lane = threadIdx.x & 31;
     const int64_t W = words_of(cols);
-    const int64_t kpw = rowbytes / (KIND == KIND_F8 ? 64 : 32);      // packed words per expanded row
+    const int64_t kpw = rowbytes / (16 * CPW);                       // packed words per expanded row
+    const int64_t ngroups = (kpw + 31) / 32;
+    const int64_t items = nrows * ngroups;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < nrows; f += nwarps) {
+    for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
+        const int64_t f = it / ngroups, wg = it - f * ngroups;
         const int64_t b = f / rows, r = f - b * rows;
-        const uint64_t *src = X + b * bs + r * ld;
-        uint8_t *dst = Y + f * rowbytes;
-        for (int64_t w = lane; w < kpw; w += 32) {
-            const uint64_t x = (w < W) ? (src[w] & word_mask(w, cols)) : 0ull;
-            if (KIND == KIND_F8) {
-                uint4 *o = reinterpret_cast<uint4 *>(dst + w * 64);
+        const int64_t w = wg * 32 + lane;
+        const uint64_t x = (w < W) ? (X[b * bs + r * ld + w] & word_mask(w, cols)) : 0ull;
+        uint4 *o = reinterpret_cast<uint4 *>(Y + f * rowbytes) + wg * 32 * CPW;
+        const int64_t left = (kpw - wg * 32) * CPW;                   // chunks of this row from here on
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t h = (uint32_t)(x >> (16 * q));
-                    o[q] = make_uint4(f8_of_nibble(h & 15u), f8_of_nibble((h >> 4) & 15u),
-                                      f8_of_nibble((h >> 8) & 15u), f8_of_nibble((h >> 12) & 15u));
-                }
+        for (int q = 0; q < CPW; ++q) {
+            const int c = 32 * q + lane;                              // chunk of the group
+            const uint64_t xs = __shfl_sync(0xffffffffu, x, c / CPW);
+            uint4 v;
+            if (KIND == KIND_F8) {
+                const uint32_t h = (uint32_t)(xs >> (16 * (c & 3)));
+                v = make_uint4(f8_of_nibble(h & 15u), f8_of_nibble((h >> 4) & 15u), f8_of_nibble((h >> 8) & 15u),
+                               f8_of_nibble((h >> 12) & 15u));
             } else {
-                uint4 *o = reinterpret_cast<uint4 *>(dst + w * 32);
-                const uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
-                o[0] = make_uint4(f4_of_byte(lo), f4_of_byte(lo >> 8), f4_of_byte(lo >> 16), f4_of_byte(lo >> 24));
-                o[1] = make_uint4(f4_of_byte(hi), f4_of_byte(hi >> 8), f4_of_byte(hi >> 16), f4_of_byte(hi >> 24));
+                const uint32_t h = (uint32_t)(xs >> (32 * (c & 1)));
+                v = make_uint4(f4_of_byte(h), f4_of_byte(h >> 8), f4_of_byte(h >> 16), f4_of_byte(h >> 24));
             }
+            if (c < left) o[c] = v;
         }
     }
 }
@@ -415,7 +425,7 @@ int mma_launch(const TcxLaunch &L, cudaStream_t s)
     P.nkb = L.rowbytes / ROWB;
     P.tiles_m = div_up(L.m, BM);
     P.tiles_n = div_up(L.n, BN);
-    P.tiles = (int64_t)L.batch * P.tiles_m * P.tiles_n;
+    P.batch = L.batch;
     P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
     P.accumulate = L.accumulate;
     P.status = L.status;
@@ -433,7 +443,8 @@ int mma_launch(const TcxLaunch &L, cudaStream_t s)
     int dev = 0, sms = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));
     GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t grid = P.tiles < sms ? P.tiles : sms;
+    const int64_t tiles = (int64_t)P.tiles_m * P.tiles_n * P.batch;
+    const int64_t grid = tiles < sms ? tiles : sms;
     ProfScope ps(KIND == KIND_F8 ? PF_TC : PF_TC_F4, s);
     tc_mma_kernel<KIND><<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(mapA, mapB, P);
     note_launch();
@@ -458,7 +469,9 @@ int tc_expand_launch(int kind, const uint64_t *X, int64_t ld, int64_t bs, int64_
     int dev = 0, sms = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));
     GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t want = (nrows + 7) / 8;                  // 8 warps per block, one row each
+    const int64_t epr = kind == KIND_F8 ? 128 : 256;
+    const int64_t groups = nrows * ((rowbytes / ROWB * epr / 64 + 31) / 32);   // 32-word groups
+    const int64_t want = (groups + 7) / 8;                 // 8 warps per block, one group each
     const int64_t grid = std::min<int64_t>(want, (int64_t)sms * 16);
     ProfScope ps(PF_EXPAND, s);
     if (kind == KIND_F8)

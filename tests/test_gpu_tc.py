@@ -115,3 +115,4 @@ def test_tc_matches_m4rm_on_the_same_inputs(base):
     g.gf2_device_status()
     assert torch.equal(C1, C2)
     assert g.gf2_freivalds(g.mat(C1, n), g.mat(Ad, l), g.mat(Bd, n), 1000) == 0
+
