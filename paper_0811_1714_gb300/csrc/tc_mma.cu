@@ -9,11 +9,12 @@
 // Why it is exact (Section 2.3): a GF(2) dot product is an AND followed by an
 // XOR accumulation, i.e. the parity of the INTEGER dot product of the 0/1
 // vectors.  Each product of two entries is 0 or 1.0, and a K-chunk of at most
-// KCHUNK = 4096 entries sums to an integer count <= 2^12, which any
-// accumulator keeping 13 or more significant bits holds exactly (FP32 keeps
-// 24).  After each chunk the accumulator D is read from tensor memory; the
-// parity of count is the last mantissa bit of D + 2^23 (whose ulp is 1), and
-// the parities of successive chunks are XORed: the GF(2) sum over all of K.
+// 4096 (FP8) or 8192 (FP4) entries sums to an integer count <= 2^12 (2^13),
+// which any accumulator keeping 12 (13) or more significant bits holds
+// exactly, whatever the order of the additions (FP32 keeps 24).  After each chunk the accumulator D is read from
+// tensor memory; the parity of count is the last mantissa bit of D + 2^23
+// (whose ulp is 1), and the parities of successive chunks are XORed: the
+// GF(2) sum over all of K.
 //
 // Two kernels:
 //  - expand_kernel<KIND>: the packed operand rows (Section 2.1 layout, a
@@ -42,6 +43,7 @@
 #include "tcgen05.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -50,44 +52,59 @@ namespace {
 
 using namespace gf2::tc;
 
-constexpr int BM = 128;                       // tile rows (MMA M)
+constexpr int BM = 128;                       // rows of a tile per CTA (MMA M per CTA)
 constexpr int BN = 256;                       // tile columns (MMA N)
 constexpr int ROWB = 128;                     // bytes of K per operand row per stage
-constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * ROWB;            // 16 KB
-constexpr int B_BYTES = BN * ROWB;            // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int KCHUNK = 4096;                  // exact-sum bound (entries per accumulation)
+constexpr int B_BYTES = BN * ROWB;            // 32 KB: the whole B^T tile (one CTA), two halves (a pair)
 constexpr int TMA_WARP = 0, MMA_WARP = 1, EPI_WARP0 = 2, NUM_EPI_WARPS = 8;
 constexpr int NTHREADS = (EPI_WARP0 + NUM_EPI_WARPS) * 32;    // 320
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t SFA_COL = 256, SFB_COL = 320;  // FP4 scale factors (32 columns each)
-constexpr int NBARS = 2 * STAGES + 4 + 1;
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + NBARS * 8 + 16;
-static_assert(SMEM_BYTES <= 232448, "shared memory per CTA");
+
+// Per-CTA stage and ring: KBS 128-byte K blocks per stage; per block one CTA
+// holds its A tile and the whole B^T tile (48 KB), each CTA of a pair its A
+// tile and one half of the pair's B^T tile (32 KB).  The ring takes what fits
+// beside the barriers in 227 KB.
+template <int PAIR, int KBS> struct Ring {
+    static constexpr int A_SUB = A_BYTES;                                  // one K block of A
+    static constexpr int B_SUB = PAIR ? B_BYTES / 2 : B_BYTES;             // one K block of B^T
+    static constexpr int STAGE_BYTES = KBS * (A_SUB + B_SUB);
+    static constexpr int STAGES = (232448 - 1024 - 256) / STAGE_BYTES > 8 ? 8 : (232448 - 1024 - 256) / STAGE_BYTES;
+    static constexpr int NBARS = 2 * STAGES + 4 + 1;
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + NBARS * 8 + 16;
+    static_assert(STAGES >= 2 && SMEM_BYTES <= 232448, "shared memory per CTA");
+};
+constexpr int KBS_PAIR = 2, KBS_ONE = 1;      // K blocks per stage
 
 template <int KIND> struct Fmt;
 template <> struct Fmt<KIND_F8> {
     static constexpr int EPR = 128;           // entries per 128-byte row
     static constexpr int NACC = 2;            // accumulators in tensor memory
+    static constexpr int KCHUNK = 4096;       // entries per exact accumulation (sums <= 2^12)
     // D = F32 (bits 4-5 = 1), A = B = E4M3 (bits 7-9, 10-12 = 0), both
     // K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static constexpr uint32_t idesc(int M) { return (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(M >> 4) << 24); }
 };
 template <> struct Fmt<KIND_F4> {
     static constexpr int EPR = 256;
     static constexpr int NACC = 1;
+    // one accumulator: every chunk boundary idles the tensor core while the
+    // epilogue reads it out, so the chunks are twice as long (sums <= 2^13)
+    static constexpr int KCHUNK = 8192;
     // block-scaled descriptor: scale-factor ids 0 (bits 4-5, 29-30), A = B =
     // E2M1 (code 1 at bits 7-9 and 10-12), both K-major, N >> 3 at bits
     // 17-22, scale type UE8M0 (bit 23 = 1), M >> 4 at bits 24-28
-    static constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) |
-                                      ((uint32_t)(BM >> 4) << 24);
+    static constexpr uint32_t idesc(int M)
+    {
+        return (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | (1u << 23) | ((uint32_t)(M >> 4) << 24);
+    }
 };
 
 struct Params {
     int64_t m, n;            // rows of A (and of C), rows of B^T (columns of C) per product
     int64_t nkb;             // 128-byte K blocks per row
-    int tiles_m, tiles_n;
+    int tiles_m, tiles_n;    // tile rows of 128 (one CTA) or 256 (a pair) rows, tile columns of 256
     int batch;
     uint64_t *C;
     int64_t ldc, bsC;
@@ -95,28 +112,88 @@ struct Params {
     unsigned int *status;
 };
 
-template <int KIND>
+// One MMA step of 32 bytes of K: M = 128 (one CTA, cta_group::1) or M = 256
+// over the pair (cta_group::2, issued by the pair's first CTA; A rows 0-127
+// and B^T rows 0-127 from its shared memory, rows 128-255 from its peer's,
+// each CTA's accumulator rows in its own tensor memory).
+template <int KIND, int PAIR>
 __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t ad, uint64_t bd, uint32_t tmem_base, uint32_t acc)
 {
+    constexpr uint32_t ID = Fmt<KIND>::idesc(PAIR ? 2 * BM : BM);
     if (KIND == KIND_F8) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-            ::"r"(d), "l"(ad), "l"(bd), "r"(Fmt<KIND_F8>::IDESC), "r"(acc)
-            : "memory");
+        if (PAIR)
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(acc) : "memory");
+        else
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(acc) : "memory");
     } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %6, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
-            ::"r"(d), "l"(ad), "l"(bd), "r"(Fmt<KIND_F4>::IDESC), "r"(tmem_base + SFA_COL),
-              "r"(tmem_base + SFB_COL), "r"(acc)
-            : "memory");
+        if (PAIR)
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+                         "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + SFA_COL), "r"(tmem_base + SFB_COL), "r"(acc)
+                         : "memory");
+        else
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + SFA_COL), "r"(tmem_base + SFB_COL), "r"(acc)
+                         : "memory");
     }
 }
 
-// Tile t -> (batch, tile row, tile column).
+// Arrival on `bar` once this thread's MMAs so far have completed: on this
+// CTA's barrier (one CTA), or on the barrier at that offset in both CTAs of
+// the pair (ctaMask 3) or in the first one only (ctaMask 1).
+template <int PAIR>
+__device__ __forceinline__ void commit(uint32_t bar, unsigned short mask)
+{
+    if (PAIR)
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                     ::"r"(bar), "h"(mask) : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The shared::cluster address of `addr` (a shared::cta address) in the
+// cluster's CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void arrive_cluster(uint32_t cluster_bar)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// TMA copy into this CTA's shared memory that completes on a barrier of
+// either CTA of the pair (its shared::cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap *map, int x, int y, int z,
+                                                 uint32_t cluster_bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(map), "r"(x), "r"(y), "r"(z), "r"(cluster_bar)
+        : "memory");
+}
+
 __device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, int &tm, int &tn)
 {
     const int64_t per = (int64_t)P.tiles_m * P.tiles_n;
@@ -126,23 +203,56 @@ __device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, 
     tn = (int)(r - (int64_t)tm * P.tiles_n);
 }
 
-template <int KIND>
+template <int PAIR>
+__device__ __forceinline__ void alloc_tmem(uint32_t slot)
+{
+    if (PAIR) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+        tmem_alloc(slot, TMEM_COLS);
+    }
+}
+
+template <int PAIR>
+__device__ __forceinline__ void free_tmem(uint32_t taddr)
+{
+    if (PAIR)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
+    else
+        tmem_dealloc(taddr, TMEM_COLS);
+}
+
+// PAIR = 0: one CTA per 128 x 256 tile.  PAIR = 1: clusters of two CTAs per
+// 256 x 256 tile, one tcgen05.mma.cta_group::2 stream issued by the first
+// CTA; each CTA copies its 128 rows of A and its 128-row half of B^T into its
+// own shared memory, the copies of both complete on the first CTA's stage
+// barrier, the MMA commits release the stage in both CTAs, and both CTAs'
+// epilogues arrive on the first CTA's accumulator-empty barrier.
+template <int KIND, int PAIR>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Params P)
 {
+    constexpr int KBS = PAIR ? KBS_PAIR : KBS_ONE;
+    using R = Ring<PAIR, KBS>;
     constexpr int NACC = Fmt<KIND>::NACC;
-    constexpr int KB_PER_CHUNK = KCHUNK / Fmt<KIND>::EPR;
+    constexpr int SPC = Fmt<KIND>::KCHUNK / Fmt<KIND>::EPR / KBS;   // stages per K-chunk
+    constexpr int STAGES = R::STAGES;
+    constexpr int STAGE_BYTES = R::STAGE_BYTES;
+    constexpr int TILE_ROWS = PAIR ? 2 * BM : BM;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // stages sit on 1024-byte boundaries (128-byte swizzle atoms)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char *sbase = smem_raw + (base - raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sbase + STAGES * STAGE_BYTES);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + NBARS);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + R::NBARS);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const uint32_t rank = PAIR ? cluster_rank() : 0u;      // 0: the CTA that issues the MMAs
     const uint32_t bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
@@ -152,18 +262,18 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(full_bar(s), 1);            // the TMA thread's expect_tx arrival
+            mbar_init(full_bar(s), 1);            // the issuing CTA's expect_tx arrival
             mbar_init(empty_bar(s), 1);           // tcgen05.commit
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(tfull_bar(b), 1);
-            mbar_init(tempty_bar(b), NUM_EPI_WARPS);
+            mbar_init(tempty_bar(b), NUM_EPI_WARPS * (PAIR ? 2 : 1));   // every epilogue warp of the pair
         }
         mbar_init(done_bar, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == MMA_WARP) tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    if (warp == MMA_WARP) alloc_tmem<PAIR>(smem_u32(tmem_slot));
     fence_before();
     __syncthreads();
     fence_after();
@@ -178,10 +288,16 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     }
     fence_before();
     __syncthreads();
+    // the peer's copies, commits and arrivals target this CTA's barriers and
+    // tensor memory: both CTAs are set up before either issues anything
+    if (PAIR) cluster_sync();
     fence_after();
     const int64_t tiles = (int64_t)P.tiles_m * P.tiles_n * P.batch;
+    const int64_t t0 = PAIR ? blockIdx.x / 2 : blockIdx.x, tstep = PAIR ? gridDim.x / 2 : gridDim.x;
+    const int64_t nst = (P.nkb + KBS - 1) / KBS;             // stages per tile (a last partial stage
+                                                             // copies K blocks beyond the row: zeros)
 
-    // every role walks the CTA's tiles t = blockIdx.x, +gridDim.x, ...
+    // every role walks its tiles t = t0, t0 + tstep, ...
     if (warp == TMA_WARP) {
         // ------------------------------------------------------------ TMA issuer
         if (lane == 0) {
@@ -189,34 +305,55 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             asm volatile("prefetch.tensormap [%0];" ::"l"(&mapB) : "memory");
             int64_t q = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            for (int64_t t = t0; t < tiles && ok; t += tstep) {
                 int b, tm, tn;
                 tile_coords(P, t, b, tm, tn);
-                for (int64_t kb = 0; kb < P.nkb; ++kb, ++q) {
+                for (int64_t ks = 0; ks < nst; ++ks, ++q) {
                     const int s = (int)(q % STAGES);
                     if (!mbar_wait(empty_bar(s), (uint32_t)((q / STAGES) & 1) ^ 1u, P.status, abort_flag)) {
                         ok = false;
                         break;
                     }
                     const uint32_t dst = base + s * STAGE_BYTES;
-                    mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
-                    tma_load_3d(dst, &mapA, (int)(kb * ROWB), tm * BM, b, full_bar(s));
-                    tma_load_3d(dst + A_BYTES, &mapB, (int)(kb * ROWB), tn * BN, b, full_bar(s));
+                    if (PAIR) {
+                        // both CTAs' copies complete on the first CTA's barrier
+                        const uint32_t fb = cluster_addr(full_bar(s), 0);
+                        if (rank == 0) mbar_arrive_expect_tx(full_bar(s), 2 * STAGE_BYTES);
+#pragma unroll
+                        for (int j = 0; j < KBS; ++j) {
+                            const int x = (int)((ks * KBS + j) * ROWB);
+                            tma_load_3d_pair(dst + j * R::A_SUB, &mapA, x, tm * TILE_ROWS + (int)rank * BM, b, fb);
+                            tma_load_3d_pair(dst + KBS * R::A_SUB + j * R::B_SUB, &mapB, x,
+                                             tn * BN + (int)rank * (BN / 2), b, fb);
+                        }
+                    } else {
+                        mbar_arrive_expect_tx(full_bar(s), STAGE_BYTES);
+#pragma unroll
+                        for (int j = 0; j < KBS; ++j) {
+                            const int x = (int)((ks * KBS + j) * ROWB);
+                            const uint32_t db = dst + KBS * R::A_SUB + j * R::B_SUB;
+                            tma_load_3d(dst + j * R::A_SUB, &mapA, x, tm * BM, b, full_bar(s));
+                            tma_load_3d(db, &mapB, x, tn * BN, b, full_bar(s));
+                            tma_load_3d(db + B_BYTES / 2, &mapB, x, tn * BN + BN / 2, b, full_bar(s));
+                        }
+                    }
                 }
             }
             // wind down: copies issued but not consumed (only after an abort)
             // still land in shared memory; wait for them before the CTA exits
-            for (int64_t r = (q > STAGES ? q - STAGES : 0); r < q; ++r)
-                mbar_drain(full_bar((int)(r % STAGES)), (uint32_t)((r / STAGES) & 1), P.status);
+            // (the issuing CTA's barriers see both CTAs' copies)
+            if (rank == 0)
+                for (int64_t r = (q > STAGES ? q - STAGES : 0); r < q; ++r)
+                    mbar_drain(full_bar((int)(r % STAGES)), (uint32_t)((r / STAGES) & 1), P.status);
         }
         __syncwarp();
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && rank == 0) {
             uint32_t it = 0, u = 0;                      // stages, accumulator uses
             bool ok = true;
-            const int nchunks = (int)((P.nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
-            for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+            const int nchunks = (int)((nst + SPC - 1) / SPC);
+            for (int64_t t = t0; t < tiles && ok; t += tstep) {
                 for (int c = 0; c < nchunks && ok; ++c, ++u) {
                     const int ab = (int)(u % NACC);
                     if (!mbar_wait(tempty_bar(ab), ((u / NACC) & 1u) ^ 1u, P.status, abort_flag)) {
@@ -225,28 +362,31 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     }
                     fence_after();
                     const uint32_t dt = tmem_base + (uint32_t)ab * 256u;
-                    const int64_t kb0 = (int64_t)c * KB_PER_CHUNK;
-                    const int64_t kb1 = std::min<int64_t>(P.nkb, kb0 + KB_PER_CHUNK);
-                    for (int64_t kb = kb0; kb < kb1; ++kb, ++it) {
+                    const int64_t ks0 = (int64_t)c * SPC;
+                    const int64_t ks1 = std::min<int64_t>(nst, ks0 + SPC);
+                    for (int64_t ks = ks0; ks < ks1; ++ks, ++it) {
                         const int s = (int)(it % STAGES);
                         if (!mbar_wait(full_bar(s), (it / STAGES) & 1u, P.status, abort_flag)) {
                             ok = false;
                             break;
                         }
                         fence_after();
-                        const uint32_t sa = base + s * STAGE_BYTES, sb = sa + A_BYTES;
+                        const uint32_t sa = base + s * STAGE_BYTES, sb = sa + KBS * R::A_SUB;
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)     // 32 bytes of K per instruction
-                            mma_issue<KIND>(dt, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
-                                            tmem_base, (kb > kb0 || kk > 0) ? 1u : 0u);
-                        mma_commit(empty_bar(s));           // stage free once these MMAs have read it
+                        for (int j = 0; j < KBS; ++j)
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
+                                mma_issue<KIND, PAIR>(dt, smem_desc_sw128(sa + j * R::A_SUB + kk * 32),
+                                                      smem_desc_sw128(sb + j * R::B_SUB + kk * 32), tmem_base,
+                                                      (ks > ks0 || j > 0 || kk > 0) ? 1u : 0u);
+                        commit<PAIR>(empty_bar(s), 3);     // stage free (in both CTAs) once these MMAs read it
                     }
                     if (!ok) break;
-                    mma_commit(tfull_bar(ab));              // accumulator ready for the epilogue
+                    commit<PAIR>(tfull_bar(ab), 3);        // accumulator ready for the epilogue(s)
                 }
             }
             // wind down: wait until every issued MMA has completed
-            mma_commit(done_bar);
+            commit<PAIR>(done_bar, 1);
             mbar_drain(done_bar, 0, P.status);
         }
         __syncwarp();
@@ -254,11 +394,11 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;                   // TMEM lanes 32*quarter.. = tile rows
         const int half = (warp - EPI_WARP0) >> 2;       // columns 128*half ..
-        const int row_in_tile = quarter * 32 + lane;
-        const int nchunks = (int)((P.nkb + KB_PER_CHUNK - 1) / KB_PER_CHUNK);
+        const int row_in_tile = (int)rank * BM + quarter * 32 + lane;
+        const int nchunks = (int)((nst + SPC - 1) / SPC);
         const int64_t nW = words_of(P.n);
         uint32_t u = 0;
-        for (int64_t t = blockIdx.x; t < tiles && !warp_aborted(abort_flag); t += gridDim.x) {
+        for (int64_t t = t0; t < tiles && !warp_aborted(abort_flag); t += tstep) {
             int b, tm, tn;
             tile_coords(P, t, b, tm, tn);
             uint32_t par[4] = {0u, 0u, 0u, 0u};
@@ -281,13 +421,16 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 // the accumulator is in registers: hand it back to the MMA
                 fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(tempty_bar(ab));
+                if (lane == 0) {
+                    if (PAIR) arrive_cluster(cluster_addr(tempty_bar(ab), 0));
+                    else mbar_arrive(tempty_bar(ab));
+                }
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     uint32_t word = 0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        // D = count <= 2^12, an integer: the ulp of D + 2^23 is 1
+                        // D = count <= 2^13, an integer: the ulp of D + 2^23 is 1
                         const uint32_t f = __float_as_uint(__uint_as_float(r[32 * g + j]) + 8388608.0f);
                         word |= (f & 1u) << j;
                     }
@@ -295,7 +438,7 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                 }
             }
             if (!ok) break;
-            const int64_t grow = (int64_t)tm * BM + row_in_tile;
+            const int64_t grow = (int64_t)tm * TILE_ROWS + row_in_tile;
             if (grow < P.m) {
                 uint64_t *C = P.C + (int64_t)b * P.bsC + grow * P.ldc;
 #pragma unroll
@@ -312,8 +455,11 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
     fence_before();
     __syncthreads();
+    // the peer may still copy into this CTA's shared memory, arrive on its
+    // barriers or be written by the pair's MMAs until both have drained
+    if (PAIR) cluster_sync();
     fence_after();
-    if (warp == MMA_WARP) tmem_dealloc(tmem_base, TMEM_COLS);
+    if (warp == MMA_WARP) free_tmem<PAIR>(tmem_base);
 }
 
 // 4 bits -> 4 bytes of 0x00 / 0x38 (E4M3 1.0): the multiply places bit i of
@@ -417,13 +563,79 @@ int make_map(CUtensorMap *map, const uint8_t *base, int64_t rowbytes, int64_t ro
     return r == CUDA_SUCCESS ? GF2_OK : GF2_ECUDA;
 }
 
+bool pairs_disabled()
+{
+    const char *e = getenv("GF2_TC_PAIRS");
+    return e && e[0] == '0';
+}
+
+template <int KIND, int PAIR>
+int mma_launch_v(const CUtensorMap &mapA, const CUtensorMap &mapB, const Params &P, int sms, cudaStream_t s)
+{
+    constexpr int SMEM = Ring<PAIR, PAIR ? KBS_PAIR : KBS_ONE>::SMEM_BYTES;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    static int max_clusters = 0;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(tc_mma_kernel<KIND, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (attr_err == cudaSuccess && PAIR) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)(sms / 2 * 2));
+            cfg.blockDim = dim3(NTHREADS);
+            cfg.dynamicSmemBytes = SMEM;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            if (cudaOccupancyMaxActiveClusters(&max_clusters, tc_mma_kernel<KIND, PAIR>, &cfg) != cudaSuccess) {
+                cudaGetLastError();
+                max_clusters = 0;
+            }
+        }
+    });
+    if (attr_err != cudaSuccess) return GF2_ECUDA;
+    if (PAIR && max_clusters < 1) return GF2_EUNSUPPORTED;
+    const int64_t tiles = (int64_t)P.tiles_m * P.tiles_n * P.batch;
+    ProfScope ps(KIND == KIND_F8 ? PF_TC : PF_TC_F4, s);
+    if (!PAIR) {
+        const int64_t grid = tiles < sms ? tiles : sms;
+        tc_mma_kernel<KIND, PAIR><<<(unsigned)grid, NTHREADS, SMEM, s>>>(mapA, mapB, P);
+    } else {
+        const int64_t clusters = std::min<int64_t>(tiles, max_clusters);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(clusters * 2));
+        cfg.blockDim = dim3(NTHREADS);
+        cfg.dynamicSmemBytes = SMEM;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        GF2_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_mma_kernel<KIND, PAIR>, mapA, mapB, P));
+    }
+    note_launch();
+    return check_launch();
+}
+
 template <int KIND>
 int mma_launch(const TcxLaunch &L, cudaStream_t s)
 {
+    int dev = 0, sms = 0;
+    GF2_CUDA_TRY(cudaGetDevice(&dev));
+    GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // pairs of CTAs on 256-row tiles wherever there are at least two 128-row
+    // tile rows; single CTAs otherwise (or with GF2_TC_PAIRS=0)
+    const bool pair = L.m > BM && !pairs_disabled();
     Params P;
     P.m = L.m; P.n = L.n;
     P.nkb = L.rowbytes / ROWB;
-    P.tiles_m = div_up(L.m, BM);
+    P.tiles_m = div_up(L.m, pair ? 2 * BM : BM);
     P.tiles_n = div_up(L.n, BN);
     P.batch = L.batch;
     P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
@@ -432,23 +644,14 @@ int mma_launch(const TcxLaunch &L, cudaStream_t s)
     CUtensorMap mapA, mapB;
     int rc = make_map(&mapA, L.XA, L.rowbytes, L.m, L.batch, BM);
     if (rc) return rc;
-    rc = make_map(&mapB, L.XB, L.rowbytes, L.n, L.batch, BN);
+    rc = make_map(&mapB, L.XB, L.rowbytes, L.n, L.batch, BN / 2);     // B^T tiles as 128-row halves
     if (rc) return rc;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(tc_mma_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    });
-    if (attr_err != cudaSuccess) return GF2_ECUDA;
-    int dev = 0, sms = 0;
-    GF2_CUDA_TRY(cudaGetDevice(&dev));
-    GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t tiles = (int64_t)P.tiles_m * P.tiles_n * P.batch;
-    const int64_t grid = tiles < sms ? tiles : sms;
-    ProfScope ps(KIND == KIND_F8 ? PF_TC : PF_TC_F4, s);
-    tc_mma_kernel<KIND><<<(unsigned)grid, NTHREADS, SMEM_BYTES, s>>>(mapA, mapB, P);
-    note_launch();
-    return check_launch();
+    if (pair) {
+        rc = mma_launch_v<KIND, 1>(mapA, mapB, P, sms, s);
+        if (rc != GF2_EUNSUPPORTED) return rc;
+        P.tiles_m = div_up(L.m, BM);
+    }
+    return mma_launch_v<KIND, 0>(mapA, mapB, P, sms, s);
 }
 
 }  // namespace

@@ -51,8 +51,10 @@ def test_tc_base_case_parity(m, l, n, base):
 
 
 @pytest.mark.parametrize("base", TCS)
-@pytest.mark.parametrize("l", [4095, 4096, 4097, 8192, 12345])
+@pytest.mark.parametrize("l", [4095, 4096, 4097, 8191, 8192, 8193, 12345, 16385])
 def test_tc_all_ones_at_the_chunk_bound(l, base):
+    """K-chunks of 4096 (FP8) and 8192 (FP4) entries: every dot product is
+    the chunk's full count, the largest sum an accumulation holds."""
     m, n = 256, 512
     A = synth.pack_bits(np.ones((m, l), np.uint8))
     B = synth.pack_bits(np.ones((l, n), np.uint8))
@@ -61,14 +63,14 @@ def test_tc_all_ones_at_the_chunk_bound(l, base):
 
 
 @pytest.mark.parametrize("base", TCS)
-@pytest.mark.parametrize("l", [4096, 6144, 9000])
+@pytest.mark.parametrize("l", [4096, 6144, 8192, 9000, 16400])
 def test_tc_staircase_sums(l, base):
     """A all ones, column j of B ones in rows 0..c_j - 1 with c_j running over
     0..l: entry (i, j) of C is c_j mod 2.  Every count up to l occurs, so
     every partial sum of a K-chunk has its low bits exercised."""
     m, n = 130, 520
     c = (np.arange(n) * 4099) % (l + 1)
-    c[:3] = [l, l - 1, 4095 if l > 4095 else 1]
+    c[:5] = [l, l - 1, 4095 if l > 4095 else 1, min(l, 8191), min(l, 8193)]
     Bb = (np.arange(l)[:, None] < c[None, :]).astype(np.uint8)
     A = synth.pack_bits(np.ones((m, l), np.uint8))
     B = synth.pack_bits(Bb)
@@ -116,3 +118,15 @@ def test_tc_matches_m4rm_on_the_same_inputs(base):
     assert torch.equal(C1, C2)
     assert g.gf2_freivalds(g.mat(C1, n), g.mat(Ad, l), g.mat(Bd, n), 1000) == 0
 
+
+
+@pytest.mark.parametrize("base", TCS)
+@pytest.mark.parametrize("m,l,n", [(300, 700, 500), (1024, 1000, 1100), (129, 4097, 260)])
+def test_tc_single_cta_tiles(m, l, n, base, monkeypatch):
+    """The same products with one CTA per 128-row tile (GF2_TC_PAIRS=0) instead
+    of pairs of CTAs that run one M = 256 MMA stream over both."""
+    monkeypatch.setenv("GF2_TC_PAIRS", "0")
+    A = synth.random_packed(m, l, 31)
+    B = synth.random_packed(l, n, 32)
+    ref = oracle.mul_packed(A, B, m, l, n)
+    assert_same_bits(tc_mul(A, B, m, l, n, base=base), ref, n, "single-CTA tc %d %s" % (base, (m, l, n)))
