@@ -119,6 +119,7 @@ def ncu_traffic(fam, leaves, M, L, N):
         return None
     return ent["bytes_per_operand_byte"] * operand_bytes(fam, leaves, M, L, N)
 UNIT = "bit-ops/s"
+DEFAULT_PATHS = "m4rm,tc_fp4,tc_fp8,tc_s8,tc_b1"
 
 
 def parse():
@@ -129,7 +130,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--p", type=float, default=0.5, help="density of one bits (square workload)")
-    ap.add_argument("--paths", default="m4rm,tc_fp4,tc_fp8,tc_s8,tc_b1", help="base cases to time")
+    ap.add_argument("--paths", default=DEFAULT_PATHS, help="base cases to time")
     ap.add_argument("--depth", type=int, default=-1)
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--t", type=int, default=0)
@@ -139,11 +140,12 @@ def parse():
                     help="skip the other configurations (config 1, 2, 3 at n=65536, 4, 5) after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of one CPU-oracle sample")
-    ap.add_argument("--workload", choices=["square", "batched", "chain", "sweep"], default="square",
+    ap.add_argument("--workload", choices=["square", "batched", "chain", "sweep", "sharded"], default="square",
                     help="square: the n x n product (default); batched: 4096 products, "
                          "dimensions log-uniform in [64, 2048], one persistent launch; "
                          "sweep: packed M4RM over Strassen depth x k at n = 8192, 16384, "
-                         "32768 and 20000x12000.12000x28000")
+                         "32768 and 20000x12000.12000x28000; sharded: one n x n product with "
+                         "its rows split over the ranks (torchrun), B broadcast")
     return ap.parse_args()
 
 
@@ -843,6 +845,65 @@ def run_chain(args, rank, world, local_rank):
     }
 
 
+def run_sharded(args, rank, world, local_rank):
+    """One n x n product with the rows of A and C split over the ranks and B
+    broadcast from rank 0 once per step (Section 3: C's rows are A's rows
+    times B, so no reduction).  Timed per step: the broadcast of B and every
+    rank's product of its rows; the stitching of C on rank 0 runs once
+    afterwards and is checked by Freivalds' test on every block."""
+    import torch
+    import paper_0811_1714_gb300 as g
+    from paper_0811_1714_gb300.sharded import gf2_mul_sharded, row_blocks
+
+    torch.cuda.set_device(local_rank)
+    g.build()
+    n = args.n
+    r0, r1 = row_blocks(n, world)[rank]
+    rows = r1 - r0
+    A = g.empty(rows, n)
+    B = g.empty(n, n)
+    if rows:
+        g.gf2_random(g.mat(A, n), 1 + 100 * rank)
+    if rank == 0:
+        g.gf2_random(g.mat(B, n), 2)
+    o = g.opts(base=BASE_OF[args.paths.split(",")[0]](g) if args.paths != DEFAULT_PATHS else g.GF2_BASE_AUTO,
+               depth=args.depth)
+    group = None
+    import torch.distributed as dist
+    for _ in range(max(3, args.warmup)):
+        C_local, _ = gf2_mul_sharded(A, B, n, n, options=o, gather=False)
+    torch.cuda.synchronize()
+    dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as cs:
+        t0 = time.time()
+        e0.record(stream)
+        for _ in range(args.steps):
+            C_local, _ = gf2_mul_sharded(A, B, n, n, options=o, gather=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.time()
+    ms, ops, value = aggregate(e0.elapsed_time(e1) / args.steps, 2.0 * rows * n * n)
+    bad = g.gf2_freivalds(g.mat(C_local, n), g.mat(A, n), g.mat(B, n), 1000 + rank) if rows else 0
+    bad_t = torch.tensor([float(bad)], device="cuda")
+    dist.all_reduce(bad_t)
+    _, C = gf2_mul_sharded(A, B, n, n, options=o, gather=True)
+    return {
+        "metric": "effective GF(2) bit-ops/s (2mnk/t), one product sharded by rows", "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "auto", "data": "synthetic: SplitMix64 bits, B seed 2, row blocks of A seeds 1+100*rank",
+        "config": {"workload": "square C=A*B over GF(2), m=l=n=%d, rows of A and C split over %d ranks, "
+                               "B broadcast once per step" % (n, world),
+                   "rows_per_rank": [b1 - b0 for b0, b1 in row_blocks(n, world)],
+                   "plan_rank0": g.gf2_describe_plan(rows, n, n, o) if rows else None},
+        "clocks": cs.summary(t0, t1),
+        "verified": {"freivalds_mismatched_rows_all_ranks": int(bad_t.item()),
+                     "stitched_rows": int(C.shape[0]) if C is not None else None},
+    }
+
+
 def run_sweep(args, rank, world, local_rank):
     """Packed M4RM over Strassen-Winograd depth (the cutoff) x k (bits per
     table; t automatic) on the square 8192, 16384 and 32768 products and on
@@ -908,8 +969,14 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    if args.workload in ("batched", "chain", "sweep"):
-        run = {"batched": run_batched, "chain": run_chain, "sweep": run_sweep}[args.workload]
+    if args.workload == "sharded" and world == 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % int(os.environ.get("MASTER_PORT", "29533")),
+                                rank=0, world_size=1)
+    if args.workload in ("batched", "chain", "sweep", "sharded"):
+        run = {"batched": run_batched, "chain": run_chain, "sweep": run_sweep, "sharded": run_sharded}[args.workload]
         line = run(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)
