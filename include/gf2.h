@@ -306,9 +306,7 @@ int gf2_profile_enable(int32_t on);
  *   4 transpose, 5 generator, 6 Freivalds products, 7 MakeTable
  *   (Algorithm 1), 8 batched base case, 9 int8 tensor-core base case,
  *   10 binary tensor-core base case, 11 FP4 tensor-core base case,
- *   12 expansion of packed operands to FP8 / FP4 entries, 13 FP8 tensor-core
- *   kernel of the batched form (packed operands expanded on chip)
- *   (Section 2.3).
+ *   12 expansion of packed operands to FP8 / FP4 entries (Section 2.3).
  */
 int gf2_profile_read(int32_t family, double *ms, int64_t *launches);
 

@@ -381,8 +381,7 @@ def gf2_profile_name(family: int):
 
 
 PROFILE_FAMILIES = ("m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose", "random",
-                    "freivalds", "make_table", "batched", "tc_s8", "tc_b1", "tc_fp4", "expand",
-                    "tc_fp8_packed")
+                    "freivalds", "make_table", "batched", "tc_s8", "tc_b1", "tc_fp4", "expand")
 
 
 # ---- torch conveniences ----------------------------------------------------

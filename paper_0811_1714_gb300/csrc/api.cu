@@ -319,8 +319,7 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
         L.C = C; L.ldc = ldc; L.bsC = bsC;
         L.m = m; L.l = l; L.n = n; L.batch = batch; L.accumulate = accumulate;
         L.status = nullptr;
-        return p.base == GF2_BASE_TC_S8 ? tc_s8_launch(L, s)
-               : p.base == GF2_BASE_TC_B1 ? tc_b1_launch(L, s) : tc_fp8_launch(L, s);
+        return p.base == GF2_BASE_TC_S8 ? tc_s8_launch(L, s) : tc_b1_launch(L, s);
     }
     M4rmLaunch L;
     L.A = A; L.lda = lda; L.bsA = bsA;
@@ -376,13 +375,12 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         }
     }
     if (b_ready) GF2_CUDA_TRY(cudaStreamWaitEvent(s, b_ready, 0));
-    // every tensor-core base case of gf2_mul reads B^T in natural bit order
-    const bool rev32 = false;
+    // the tensor-core base cases read B transposed
     if (tc) {
         uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
         DMat T{Bt, n, l, p.ldBt};
         DMat X{B->data, l, n, B->stride_words};
-        int rc = transpose_launch(T, X, s, rev32);
+        int rc = transpose_launch(T, X, s);
         if (rc) return rc;
         Bsrc = Bt;
         ldBsrc = p.ldBt;
@@ -417,11 +415,8 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
             // (B_SW)^T and SW is (B_NE)^T; side 2 swaps their roles
             SB.side = 2; SB.rows = Np; SB.cols = Lp;
             if (j == 1) {
-                // the tail beyond l is zero already; with reversed halves a
-                // mask at column l would cut the wrong bits, so the split
-                // takes whole words
                 SB.X = Bsrc; SB.ld = ldBsrc; SB.bs = 0; SB.vrows = n;
-                SB.vcols = rev32 ? words_of(l) * 64 : l;
+                SB.vcols = l;
             } else {
                 SB.X = reinterpret_cast<const uint64_t *>(scratch + p.offB[j - 1]);
                 SB.ld = p.ldB[j - 1]; SB.bs = p.slabB[j - 1]; SB.vrows = Np; SB.vcols = Lp;
@@ -899,7 +894,7 @@ const char *gf2_profile_name(int32_t family)
 {
     static const char *names[PF_COUNT] = {"m4rm", "tc_fp8", "sw_split", "sw_combine", "transpose",
                                           "random", "freivalds", "make_table", "batched", "tc_s8", "tc_b1",
-                                          "tc_fp4", "expand", "tc_fp8_packed"};
+                                          "tc_fp4", "expand"};
     if (family < 0 || family >= PF_COUNT) return nullptr;
     return names[family];
 }
@@ -1075,7 +1070,7 @@ int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[], const gf2_m
             bc.push_back(C[i]);
             ba.push_back(A[i]);
             bb.push_back(B[i]);
-        } else if (base == GF2_BASE_TC_FP8 && depth == 0 && tc_fp8_available()) {
+        } else if (is_expanded(base) && depth == 0 && tc_fp8_available()) {
             tcc.push_back(C[i]);
             tca.push_back(A[i]);
             tcb.push_back(B[i]);
@@ -1085,7 +1080,8 @@ int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[], const gf2_m
         }
     }
     if (!tcc.empty()) {
-        rc = gf2::tc_batched_mul(tcc.data(), tca.data(), tcb.data(), (int)tcc.size(), o.accumulate, s);
+        rc = gf2::tc_batched_mul(tcc.data(), tca.data(), tcb.data(), (int)tcc.size(), o.accumulate,
+                                 kind_of(o.base), s);
         if (rc) return rc;
     }
     if (bc.empty()) return GF2_OK;

@@ -40,7 +40,7 @@ void note_launch(int n = 1);
 
 // Kernel families for the device-time accounting of gf2_profile_*.
 enum ProfFamily { PF_M4RM = 0, PF_TC, PF_SPLIT, PF_COMBINE, PF_TRANSPOSE, PF_RANDOM, PF_MATVEC,
-                  PF_TABLE, PF_BATCHED, PF_TC_S8, PF_TC_B1, PF_TC_F4, PF_EXPAND, PF_TC_PACKED, PF_COUNT };
+                  PF_TABLE, PF_BATCHED, PF_TC_S8, PF_TC_B1, PF_TC_F4, PF_EXPAND, PF_COUNT };
 
 // Brackets the launches made during its lifetime with CUDA events on `s`
 // when accounting is on.
@@ -111,8 +111,8 @@ int sw_combine2_launch(const CombineLaunch &L, cudaStream_t s);
 
 // Utilities.
 int random_launch(DMat M, uint64_t seed, double p, cudaStream_t s);
-// T = X^T; rev32: the bits of each 32-bit half of T's words reversed
-int transpose_launch(DMat T, DMat X, cudaStream_t s, bool rev32 = false);
+// T = X^T
+int transpose_launch(DMat T, DMat X, cudaStream_t s);
 int zero_launch(DMat M, cudaStream_t s);   // clears rows x stride words
 // Y (rows words) = M X with X one word per column of M (64 vectors).
 int matvec64_launch(const uint64_t *M, int64_t rows, int64_t cols, int64_t ld,
@@ -121,7 +121,8 @@ int xor_count_launch(const uint64_t *a, const uint64_t *b, int64_t n,
                      unsigned long long *count, cudaStream_t s);
 int seeded_words_launch(uint64_t *X, int64_t n, uint64_t seed, cudaStream_t s);
 
-// Tensor-core base case (FP8 e4m3 0/1 operands, exact FP32 sums, parity).
+// Warp-level tensor-core base cases (mma.sync on 0/1 int8 or packed 1-bit
+// operands, int32 sums, parity).
 struct TcLaunch {
     const uint64_t *A; int64_t lda, bsA;     // m x l
     const uint64_t *Bt; int64_t ldb, bsB;    // n x l (B transposed)
@@ -131,7 +132,6 @@ struct TcLaunch {
     int accumulate;
     unsigned int *status;                    // device word for timeouts (may be null)
 };
-int tc_fp8_launch(const TcLaunch &L, cudaStream_t s);
 // Device status word of the tensor-core kernels' bounded waits.
 int tc_status_address(unsigned int **p);
 
@@ -179,10 +179,11 @@ const char *batched_variant_name(int i);
 void batched_release();
 int tc_status_read_and_clear(unsigned int *out, cudaStream_t s);
 int wait_selftest_launch(long long limit, cudaStream_t s);
-// Batched products of uneven shapes on the tensor-core base case (one
-// batched transpose + one persistent launch, graph-replayed).
+// Batched products of uneven shapes on a tcgen05 base case of `kind` (one
+// batched transpose, one batched expansion and one persistent launch,
+// graph-replayed).
 int tc_batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *const B[], int count,
-                   int accumulate, cudaStream_t s);
+                   int accumulate, int kind, cudaStream_t s);
 void tc_batched_release();
 bool tc_fp8_available();
 

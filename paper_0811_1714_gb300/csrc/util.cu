@@ -1,5 +1,4 @@
-// util.cu -- device helpers: seeded bit generator, bit transpose (optionally
-// with bit-reversed 32-bit halves, the FP8 base case's order), the packed
+// util.cu -- device helpers: seeded bit generator, bit transpose, the packed
 // matrix-vector product used by Freivalds' check, the cubic product of
 // Section 2.3 for right factors of at most 64 columns, launch bookkeeping and
 // device-time accounting.
@@ -142,10 +141,8 @@ __global__ void seeded_words_kernel(uint64_t *X, int64_t n, uint64_t seed)
 }
 
 // T = X^T, one warp per 64 x 64 block: lane i holds rows i and i+32 of the
-// block; a ballot over the lanes of bit j gathers column j.  With rev32 the
-// bits of each 32-bit half of every output word are stored reversed (bit b
-// of the half at 31 - b), the order the FP8 tensor-core base case expands.
-__global__ void transpose_kernel(DMat T, DMat X, int rev32)
+// block; a ballot over the lanes of bit j gathers column j.
+__global__ void transpose_kernel(DMat T, DMat X)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -175,10 +172,6 @@ __global__ void transpose_kernel(DMat T, DMat X, int rev32)
         const uint64_t tm = word_mask(rb, T.cols);
         out0 &= tm;
         out1 &= tm;
-        if (rev32) {
-            out0 = ((uint64_t)__brev((uint32_t)(out0 >> 32)) << 32) | __brev((uint32_t)out0);
-            out1 = ((uint64_t)__brev((uint32_t)(out1 >> 32)) << 32) | __brev((uint32_t)out1);
-        }
         const int64_t t0 = cb * 64 + lane, t1 = t0 + 32;
         if (t0 < T.rows) T.p[t0 * T.ld + rb] = out0;
         if (t1 < T.rows) T.p[t1 * T.ld + rb] = out1;
@@ -296,14 +289,14 @@ int seeded_words_launch(uint64_t *X, int64_t n, uint64_t seed, cudaStream_t s)
     return check_launch();
 }
 
-int transpose_launch(DMat T, DMat X, cudaStream_t s, bool rev32)
+int transpose_launch(DMat T, DMat X, cudaStream_t s)
 {
     const int64_t nblk = ((X.rows + 63) / 64) * words_of(X.cols);
     if (nblk <= 0) return GF2_OK;
     int64_t blocks = (nblk * 32 + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
     ProfScope ps(PF_TRANSPOSE, s);
-    transpose_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, X, rev32 ? 1 : 0);
+    transpose_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, X);
     note_launch();
     return check_launch();
 }

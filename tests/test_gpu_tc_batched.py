@@ -1,5 +1,6 @@
-"""The batched form on the tensor-core base case: many products of uneven
-shapes in one batched transpose and one persistent tensor-core launch.
+"""The batched form on the tcgen05 base cases (FP8 and FP4): many products of
+uneven shapes in one batched transpose, one batched expansion and one
+persistent tensor-core launch.
 
 Bit-exact against the CPU oracle on ragged batches (tails in every
 dimension, K extents across the exact-sum chunk bound, accumulate mode,
@@ -19,8 +20,9 @@ pytestmark = pytest.mark.gpu
 
 import paper_0811_1714_gb300 as g  # noqa: E402
 
-TC = g.GF2_BASE_TC_FP8
-TC0 = dict(base=TC, depth=0)
+@pytest.fixture(params=[g.GF2_BASE_TC_FP8, g.GF2_BASE_TC_FP4], ids=["fp8", "fp4"])
+def TC0(request):
+    return dict(base=request.param, depth=0)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -73,23 +75,23 @@ RAGGED = [(1, 1, 1), (128, 128, 256), (65, 63, 129), (300, 700, 100), (1000, 90,
           (130, 4097, 300), (200, 9000, 70)]
 
 
-def test_tc_batched_ragged():
+def test_tc_batched_ragged(TC0):
     b = make_batch(RAGGED, 700)
     g.gf2_mul_batched(b["arrs"], options=g.opts(**TC0))
     g.gf2_device_status()
     check_batch(b, RAGGED, "tc batched")
 
 
-def test_tc_batched_accumulate():
+def test_tc_batched_accumulate(TC0):
     b = make_batch(RAGGED, 710, C0_seed=9000)
     g.gf2_mul_batched(b["arrs"], options=g.opts(accumulate=1, **TC0))
     g.gf2_device_status()
     check_batch(b, RAGGED, "tc batched accumulate")
 
 
-def test_tc_batched_all_ones_chunk_bound():
+def test_tc_batched_all_ones_chunk_bound(TC0):
     """All-ones operands: every dot product equals K, the largest chunk sum."""
-    dims = [(256, 4096, 512), (130, 4097, 300), (64, 8192, 64)]
+    dims = [(256, 4096, 512), (130, 4097, 300), (64, 8192, 64), (64, 8193, 70), (129, 16385, 64)]
     hostA = [synth.pack_bits(np.ones((m, l), np.uint8)) for m, l, n in dims]
     hostB = [synth.pack_bits(np.ones((l, n), np.uint8)) for m, l, n in dims]
     dA, dB, dC = [to_dev(x) for x in hostA], [to_dev(x) for x in hostB], [g.empty(m, n) for m, l, n in dims]
@@ -103,7 +105,7 @@ def test_tc_batched_all_ones_chunk_bound():
         assert_same_bits(to_host(dC[i]), expect, n, "ones %s" % ((m, l, n),))
 
 
-def test_tc_batched_empty_products_and_replay():
+def test_tc_batched_empty_products_and_replay(TC0):
     """Empty products beside real ones; the second call replays the cached
     graph on new contents and must clear the K = 0 products again."""
     dims = [(70, 0, 90), (0, 50, 40), (60, 50, 0), (300, 500, 200), (129, 4100, 257)]
@@ -122,12 +124,12 @@ def test_tc_batched_empty_products_and_replay():
     before = g.gf2_launch_count()
     g.gf2_mul_batched(b["arrs"], options=o)
     g.gf2_device_status()
-    assert g.gf2_launch_count() - before == 2          # batched transpose + product kernel
+    assert g.gf2_launch_count() - before == 3          # batched transpose, expansion, product kernel
     check_batch(b, dims, "tc replay")
     assert not to_host(b["dC"][0]).any()
 
 
-def test_tc_batched_matches_m4rm_batched():
+def test_tc_batched_matches_m4rm_batched(TC0):
     dims = synth.batch_dims(40, seed=11, lo=32, hi=1500)
     bt = make_batch(dims, 800)
     bm = make_batch(dims, 800)
@@ -139,7 +141,7 @@ def test_tc_batched_matches_m4rm_batched():
     check_batch(bt, dims[:8], "tc vs oracle")
 
 
-def test_tc_batch_of_4096_log_uniform_products():
+def test_tc_batch_of_4096_log_uniform_products(TC0):
     """4096 products, every dimension log-uniform in [64, 2048] (seeded)."""
     dims = synth.batch_dims(4096)
     MA, MB, MC, keep = [], [], [], []
