@@ -140,7 +140,8 @@ def parse():
                     help="skip the other configurations (config 1, 2, 3 at n=65536, 4, 5) after the headline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target duration of one CPU-oracle sample")
-    ap.add_argument("--workload", choices=["square", "batched", "chain", "sweep", "sharded"], default="square",
+    ap.add_argument("--workload", choices=["square", "batched", "chain", "sweep", "sharded", "peaks"],
+                    default="square",
                     help="square: the n x n product (default); batched: 4096 products, "
                          "dimensions log-uniform in [64, 2048], one persistent launch; "
                          "sweep: packed M4RM over Strassen depth x k at n = 8192, 16384, "
@@ -685,6 +686,26 @@ def run_reference(args):
     }
 
 
+def batched_table_bytes(vname, dims):
+    """Algorithmic table-row reads of a batched variant: m*l*n / (8k) bytes
+    per product for k-bit tables.  A split variant "tall-k8t2-bm1024-from<r>+
+    slots-k<k>t<t>-..." runs each product's full 1024-row blocks, and its last
+    block when that keeps at least r rows, with k = 8 and the other rows with
+    the slot kernel's k."""
+    import re
+    if "+" in vname:
+        split = int(re.search(r"-from(\d+)\+", vname).group(1))
+        k_rest = int(re.search(r"\+slots-k(\d+)t", vname).group(1))
+        total = 0.0
+        for m, l, n in dims:
+            full = m // 1024 * 1024
+            tall = m if m - full >= split else full
+            total += tall * l * n / 64.0 + (m - tall) * l * n / (8.0 * k_rest)
+        return total, "k=8 on the tall row blocks (from %d rows), k=%d on the rest" % (split, k_rest)
+    k = int(re.search(r"k(\d+)t", vname).group(1))
+    return sum(m * l * n for m, l, n in dims) / (8.0 * k), "k=%d tables" % k
+
+
 def run_batched(args, rank, world, local_rank):
     """4096 independent products, m, l, n log-uniform in [64, 2048] (seeded),
     one persistent launch replayed as a CUDA graph (autotuned variant)."""
@@ -737,18 +758,17 @@ def run_batched(args, rank, world, local_rank):
     bad = sampled_bad(5)
     peaks, peak_kind = load_peaks()
     vname = g.gf2_batched_variant_name(variant)
-    kbits = int(vname.split("-k")[1][0]) if "-k" in vname else (int(vname[1]) if vname.startswith("k") else 8)
-    # table-row reads of the k-bit tables: m*l*n / (8k) bytes per product
     rl = None
     if k_n:
         per_launch_ms = k_ms / k_n
-        smem_bytes = sum(m * l * n for m, l, n in dims) / (8.0 * kbits)
+        smem_bytes, note_k = batched_table_bytes(vname, dims)
         achieved = smem_bytes / (per_launch_ms * 1e-3) / 1e9
         peak, note = smem_peak(peaks)
         rl = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
               "traffic": None, "kernel_ms_per_launch": per_launch_ms,
               "peak_note": note,
-              "work_note": "table-row reads of k=%d tables, sum of m*l*n/(8k) over the 4096 products" % kbits}
+              "work_note": "table-row reads, sum of m*l*n/(8k) over the 4096 products (%s); "
+                           "time of the whole graph" % note_k}
     ms, ops_all, value = aggregate(ms_local, ops)
     # the same batch on the tcgen05 base cases: one batched transpose, one
     # batched expansion and one persistent tensor-core launch per step
@@ -962,6 +982,26 @@ def run_sweep(args, rank, world, local_rank):
     }
 
 
+def run_peaks(args, rank, world, local_rank):
+    """The throughput probes behind the peaks that MEASURED_PEAKS.json does
+    not hold (shared-memory lookups, L2, mma.sync, tcgen05 MMA-only), run as
+    the package's probe executable, with the clocks sampled around it."""
+    import subprocess
+    import paper_0811_1714_gb300 as g
+    from paper_0811_1714_gb300 import buildlib
+    g.build()
+    exe = buildlib.probe_path("peaks")
+    with ClockSampler(local_rank) as cs:
+        t0 = time.time()
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=600)
+        t1 = time.time()
+    if r.returncode != 0:
+        raise RuntimeError("peak probes failed (%d): %s %s" % (r.returncode, r.stdout[-2000:], r.stderr[-2000:]))
+    probes = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"workload": "peaks", "probes": probes, "clocks": cs.summary(t0, t1),
+            "note": "CUDA-event time of the second of two identical launches per probe"}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -982,8 +1022,9 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % int(os.environ.get("MASTER_PORT", "29533")),
                                 rank=0, world_size=1)
-    if args.workload in ("batched", "chain", "sweep", "sharded"):
-        run = {"batched": run_batched, "chain": run_chain, "sweep": run_sweep, "sharded": run_sharded}[args.workload]
+    if args.workload in ("batched", "chain", "sweep", "sharded", "peaks"):
+        run = {"batched": run_batched, "chain": run_chain, "sweep": run_sweep, "sharded": run_sharded,
+               "peaks": run_peaks}[args.workload]
         line = run(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)

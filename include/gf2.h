@@ -169,9 +169,11 @@ int gf2_mul_batched(gf2_mat *const C[], const gf2_mat *const A[],
  * used.  Details of the batched form:
  *  - products whose automatic plan recurses (every dimension >= 8192) or that
  *    request depth > 0 or the tensor-core base are run one by one as gf2_mul;
- *    all others go into ONE persistent launch of the packed M4RM kernel
- *    whose CTAs pull tiles of all products from one work queue, longest K
- *    first;
+ *    all others go into ONE CUDA graph of persistent launches of the packed
+ *    M4RM kernel whose CTAs pull tiles of all products from one work queue,
+ *    longest K first: one launch, or two for the split variants (the tall
+ *    k = 8 slot kernel over the row blocks of at least r rows, then the slot
+ *    kernel over the rest);
  *  - the first call for a set of operands (pointers, shapes, strides,
  *    stream, options) times every variant on that batch (the autotuner),
  *    keeps the fastest, and builds a CUDA graph {reset the queue, launch};
@@ -189,8 +191,12 @@ int gf2_mul_batched_ex(gf2_mat *const C[], const gf2_mat *const A[],
  * tables (k bits, Section 3.1; t tables, Section 3.3) x tile width x rows. */
 int32_t gf2_batched_variant_count(void);
 
-/* Name of one batched tile variant, "k<k>t<t>-w<columns>-bm<rows>" with k
- * and t as in Sections 3.1 and 3.3 (NULL beyond the last). */
+/* Name of one batched tile variant (NULL beyond the last), with k and t as
+ * in Sections 3.1 and 3.3: "k<k>t<t>-w<columns>-bm<rows>" (one product per
+ * tile), "slots-k<k>t<t>-bm<rows>" (8 products' 128-column slices per tile),
+ * "tall-k8t2-bm1024" (slot tiles of 1024 rows), and
+ * "tall-k8t2-bm1024-from<r>+slots-..." (row blocks of at least r rows on the
+ * tall kernel, the rest on the slot kernel). */
 const char *gf2_batched_variant_name(int32_t variant);
 
 /* ---- steps of the path, callable alone ------------------------------------

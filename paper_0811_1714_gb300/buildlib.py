@@ -2,7 +2,9 @@
 
 Each .cu file of csrc/ is compiled to an object in parallel, then linked
 into paper_0811_1714_gb300/_build/libgf2.so.  A file is recompiled only when
-it, or a header, is newer than its object.
+it, or a header, is newer than its object.  Each .cu file of probes/ (the
+throughput probes behind the roofline peaks) becomes an executable
+_build/gf2_<name> in the same pass.
 """
 from __future__ import annotations
 
@@ -16,6 +18,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
+PROBES = os.path.join(HERE, "probes")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgf2.so")
@@ -50,14 +53,35 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
+def probe_path(name: str) -> str:
+    return os.path.join(OUT, "gf2_" + name)
+
+
+def _compile_probe(src: str) -> str:
+    exe = probe_path(os.path.basename(src)[:-3])
+    if os.path.exists(exe) and os.path.getmtime(exe) >= os.path.getmtime(src):
+        return exe
+    cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-o", exe + ".tmp", src]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
+    os.replace(exe + ".tmp", exe)
+    return exe
+
+
 def build(verbose: bool = False, extra: list[str] | None = None, jobs: int | None = None) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libgf2.so; returns its path."""
+    """Compile every csrc/*.cu for sm_103a and link libgf2.so (and build the
+    probes/ executables); returns the library's path."""
     os.makedirs(OUT, exist_ok=True)
     extra = list(extra or [])
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    jobs = jobs or min(len(srcs), os.cpu_count() or 4)
+    probes = sorted(glob.glob(os.path.join(PROBES, "*.cu")))
+    jobs = jobs or min(len(srcs) + len(probes), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        pfut = [ex.submit(_compile_probe, p) for p in probes]
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
+        for f in pfut:
+            f.result()
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]

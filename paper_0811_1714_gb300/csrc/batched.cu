@@ -40,6 +40,7 @@ namespace {
 
 using namespace m4rm_dev;
 
+
 struct BProd {
     const uint64_t *A;
     const uint64_t *B;
@@ -352,90 +353,262 @@ __global__ void __launch_bounds__(NW * 32) m4rm_slots_kernel(const BProd *__rest
     }
 }
 
+// Tall slot-packed tiles for k = 8 tables (Section 3.1; t tables per pass,
+// Section 3.3): the same 8 slots of 128 columns as m4rm_slots_kernel, but
+// 1024 rows per tile, so that one build of the 256-entry tables serves
+// four times as many lookups as a 256-row tile.  With t = 2 the tables take
+// 64 KB.  A is staged in 16-byte chunks per (row, slot) (128 entries of K,
+// 128 / (k t) passes) with coalescing-free 16-byte copies that bypass L1,
+// into ONE 128 KB buffer: the next chunk is copied after every warp's last
+// lookup in the current one, while the next pass builds its tables.  Each
+// thread stages one slot's rows (its slot is fixed by the thread index).
+// The tile's `rows` field is the largest row count of its slots: warps whose
+// rows all lie beyond it skip the lookups, so a tile of short row blocks
+// pays for the table build only.
+template <int KB, int NT, int R, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) m4rm_tall_slots_kernel(const BProd *__restrict__ prods,
+                                                                      const void *__restrict__ tiles_v,
+                                                                      int ntiles, unsigned int *counter,
+                                                                      int accumulate)
+{
+    constexpr int LPR = 8;
+    constexpr int NTH = NW * 32;
+    constexpr int KG = KB * NT;
+    constexpr int TROWS = 1 << KB;
+    constexpr int BM = NW * 4 * R;
+    constexpr int PPC = 128 / KG;                         // passes per staged 16-byte A chunk
+    constexpr int SROWS = NTH / LPR;                      // rows one staging sweep covers
+    constexpr unsigned IMASK = (1u << KB) - 1u;
+    static_assert(128 % KG == 0 && KG <= 32, "passes tile the 16-byte A chunks");
+    static_assert(NTH % LPR == 0 && KG * LPR <= NTH, "");
+    const PTile *tiles = static_cast<const PTile *>(tiles_v);
+
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint4 *tab = reinterpret_cast<uint4 *>(smem_raw);     // NT * TROWS * 8
+    uint4 *stg = tab + NT * TROWS * LPR;                  // 2 * KG * 8
+    uint4 *sta = stg + 2 * KG * LPR;                      // BM * 8: A chunk of (row, slot)
+    __shared__ BProd sp[8];
+    __shared__ PSlot ss[8];
+    __shared__ int s_tile;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int c = lane & 7;                               // my slot (lookups and output)
+    const int trow = warp * 4 * R + (lane >> 3);          // rows trow + 4 r
+    const int cs = tid & 7, srow = tid >> 3;              // staging: slot cs, rows srow + SROWS j
+
+    while (true) {
+        if (tid == 0) s_tile = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= ntiles) break;
+        if (tid < 8) {
+            const PSlot sl = tiles[t].slot[tid];
+            ss[tid] = sl;
+            if (sl.prod >= 0) sp[tid] = prods[sl.prod];
+        }
+        const int groups = tiles[t].groups;
+        const int rows = tiles[t].pad[0];                 // largest row count of the slots
+        __syncthreads();
+        const bool mine = ss[c].prod >= 0;
+        const int64_t my_m = mine ? sp[c].m : 0, my_l = mine ? sp[c].l : 0, my_n = mine ? sp[c].n : 0;
+        const int64_t my_row0 = ss[c].row0, my_w = ss[c].word0;
+        const uint64_t cm0 = mine ? word_mask(my_w, my_n) : 0ull, cm1 = mine ? word_mask(my_w + 1, my_n) : 0ull;
+        const uint4 cmask = make_uint4((uint32_t)cm0, (uint32_t)(cm0 >> 32), (uint32_t)cm1, (uint32_t)(cm1 >> 32));
+        const bool active = warp * 4 * R < rows;          // warp-uniform
+        // the staging thread's slot: its A rows srow + SROWS j below the slot's m
+        const bool s_mine = ss[cs].prod >= 0;
+        const int64_t s_lda = s_mine ? sp[cs].lda : 0;
+        const uint64_t *s_a = s_mine ? sp[cs].A + ((int64_t)ss[cs].row0 + srow) * s_lda : prods[0].A;
+        const int64_t s_left = s_mine ? sp[cs].m - ss[cs].row0 - srow : 0;
+        const int s_nj = s_left <= 0 ? 0 : (int)((s_left + SROWS - 1) / SROWS);
+        const int64_t s_lw = s_mine ? words_of(sp[cs].l) : 0;
+        uint4 acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+
+        auto issue_b = [&](int g, int buf) {
+            if (tid < KG * LPR) {
+                const int rr = tid >> 3, cc = tid & 7;
+                const int64_t brow = (int64_t)g * KG + rr;
+                const bool valid = ss[cc].prod >= 0 && brow < sp[cc].l && ss[cc].word0 < words_of(sp[cc].n);
+                const uint64_t *src = valid ? (sp[cc].B + brow * sp[cc].ldb + ss[cc].word0) : prods[0].B;
+                cp_async16(&stg[buf * KG * LPR + tid], src, valid);
+            }
+        };
+        // A chunk `ch`: words 2 ch, 2 ch + 1 of every staged row (rows at or
+        // past the slot's m are left as they are: their outputs are not stored)
+        auto issue_a = [&](int ch) {
+            const int64_t wa = 2 * (int64_t)ch;
+            const bool kin = wa < s_lw;
+#pragma unroll 1
+            for (int j = 0; j < s_nj; ++j) {
+                const int row = srow + SROWS * j;
+                if (row >= rows) break;
+                cp_async16(&sta[row * LPR + cs], kin ? s_a + SROWS * j * s_lda + wa : prods[0].A, kin);
+            }
+        };
+
+        if (groups > 0) {
+            issue_a(0);
+            issue_b(0, 0);
+            cp_async_commit();
+        }
+#pragma unroll 1
+        for (int g = 0; g < groups; ++g) {
+            const int buf = g & 1;
+            const bool new_chunk = g > 0 && (g % PPC) == 0;
+            cp_async_wait_all();
+            __syncthreads();                              // every warp is done with pass g - 1
+            if (new_chunk) issue_a(g / PPC);
+            if (g + 1 < groups) issue_b(g + 1, buf ^ 1);
+            cp_async_commit();
+            build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
+            if (new_chunk) cp_async_wait_all();           // this pass's A chunk (and the next B rows)
+            __syncthreads();
+            if (active) {
+                const int64_t kb = (int64_t)g * KG;
+                const int sh = (int)(kb & 63);
+                const uint64_t mlo = mine ? word_mask(kb >> 6, my_l) : 0ull;
+                const int half = (g / (64 / KG)) & 1;    // 64-bit word of the chunk
+                const uint4 *arow = sta + trow * LPR + c;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (warp * 4 * R + 4 * r < rows) {
+                        const uint2 aw = reinterpret_cast<const uint2 *>(&arow[4 * r * LPR])[half];
+                        const uint64_t bits = ((((uint64_t)aw.y << 32) | aw.x) & mlo) >> sh;
+                        uint4 a = acc[r];
+#pragma unroll
+                        for (int ti = 0; ti < NT; ++ti) {
+                            const unsigned x = (unsigned)(bits >> (ti * KB)) & IMASK;
+                            a = x4(a, tab[(ti * TROWS + (int)x) * LPR + c]);
+                        }
+                        acc[r] = a;
+                    }
+                    asm volatile("" ::: "memory");
+                }
+            }
+        }
+
+        const int64_t nW = words_of(my_n);
+        if (mine && my_w < nW) {
+            const int64_t first = my_row0 + trow;
+            const int64_t left = my_m - first;
+            const int nrows = left <= 0 ? 0 : (left < 4 * R ? (int)left : 4 * R);
+            uint64_t *cr = sp[c].C + first * sp[c].ldc + my_w;
+            const int64_t step = 4 * sp[c].ldc;
+            const bool two = my_w + 1 < nW;
+            if (!accumulate && two) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (4 * r < nrows) *reinterpret_cast<uint4 *>(cr + r * step) = and4(acc[r], cmask);
+            } else {
+#pragma unroll 1
+                for (int r = 0; r < R; ++r) {
+                    if (4 * r >= nrows) break;
+                    uint4 a = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int q = 0; q < R; ++q)
+                        if (q == r) a = acc[q];
+                    const uint64_t v0 = ((uint64_t)a.y << 32 | a.x) & cm0;
+                    const uint64_t v1 = ((uint64_t)a.w << 32 | a.z) & cm1;
+                    uint64_t *cc = cr + r * step;
+                    if (accumulate) {
+                        cc[0] ^= v0;
+                        if (two) cc[1] ^= v1;
+                    } else {
+                        cc[0] = v0;
+                    }
+                }
+            }
+        }
+        __syncthreads();    // s_tile, slot descriptors and shared buffers are reused
+    }
+}
+
 using BatchedFn = void (*)(const BProd *, const void *, int, unsigned int *, int);
 
-struct BVariant {
-    const char *name;
-    int k, t, lpr, bm, nw;
+// One kernel of a variant: its function, tile shape and dynamic shared memory.
+struct BKernel {
     BatchedFn fn;
-    int smem;
+    int k, t, lpr, bm, nw, smem;
     int packed;   // 1: slot-packed tiles (PTile), 0: one product per tile (BTile)
 };
 
+// A tile variant: one kernel over every tile, or (split > 0) the tall slot
+// kernel over the row blocks of at least `split` rows followed by `main`
+// over the rest.
+struct BVariant {
+    const char *name;
+    BKernel main;
+    int split;
+    BKernel tall;
+};
+
 template <int KB, int NT, int LPR, int R, int NW>
-BVariant make_bvariant(const char *name)
+BKernel one_kernel()
 {
     constexpr int BM = NW * (32 / LPR) * R;
-    return BVariant{name, KB, NT, LPR, BM, NW, &m4rm_batched_kernel<KB, NT, LPR, R, NW>,
-                    NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16, 0};
+    return BKernel{&m4rm_batched_kernel<KB, NT, LPR, R, NW>, KB, NT, LPR, BM, NW,
+                   NT * (1 << KB) * LPR * 16 + 2 * KB * NT * LPR * 16 + 2 * BM * 16, 0};
 }
 
 template <int KB, int NT, int R, int NW>
-BVariant make_slot_variant(const char *name)
+BKernel slot_kernel()
 {
     constexpr int BM = NW * 4 * R;
-    return BVariant{name, KB, NT, 8, BM, NW, &m4rm_slots_kernel<KB, NT, R, NW>,
-                    NT * (1 << KB) * 8 * 16 + 2 * KB * NT * 8 * 16 + 2 * BM * 8 * 16, 1};
+    return BKernel{&m4rm_slots_kernel<KB, NT, R, NW>, KB, NT, 8, BM, NW,
+                   NT * (1 << KB) * 8 * 16 + 2 * KB * NT * 8 * 16 + 2 * BM * 8 * 16, 1};
+}
+
+template <int KB, int NT, int R, int NW>
+BKernel tall_kernel()
+{
+    constexpr int BM = NW * 4 * R;
+    return BKernel{&m4rm_tall_slots_kernel<KB, NT, R, NW>, KB, NT, 8, BM, NW,
+                   NT * (1 << KB) * 8 * 16 + 2 * KB * NT * 8 * 16 + BM * 8 * 16, 1};
 }
 
 const std::vector<BVariant> &bvariants()
 {
+    static const BKernel none{};
     static const std::vector<BVariant> v = {
-        make_bvariant<8, 4, 8, 32, 8>("k8t4-w1024-bm1024"),
-        make_bvariant<6, 8, 8, 8, 8>("k6t8-w1024-bm256"),
-        make_bvariant<6, 8, 4, 8, 8>("k6t8-w512-bm512"),
-        make_bvariant<5, 8, 4, 4, 8>("k5t8-w512-bm256"),
-        make_bvariant<4, 8, 4, 4, 8>("k4t8-w512-bm256"),
-        make_bvariant<6, 8, 2, 4, 8>("k6t8-w256-bm512"),
-        make_bvariant<4, 8, 2, 2, 8>("k4t8-w256-bm256"),
-        make_bvariant<8, 4, 4, 16, 8>("k8t4-w512-bm1024"),
-        make_slot_variant<8, 4, 8, 8>("slots-k8t4-bm256"),
-        make_slot_variant<4, 8, 8, 8>("slots-k4t8-bm256"),
-        make_slot_variant<4, 8, 4, 8>("slots-k4t8-bm128"),
+        {"k8t4-w1024-bm1024", one_kernel<8, 4, 8, 32, 8>(), 0, none},
+        {"k6t8-w1024-bm256", one_kernel<6, 8, 8, 8, 8>(), 0, none},
+        {"k6t8-w512-bm512", one_kernel<6, 8, 4, 8, 8>(), 0, none},
+        {"k5t8-w512-bm256", one_kernel<5, 8, 4, 4, 8>(), 0, none},
+        {"k4t8-w512-bm256", one_kernel<4, 8, 4, 4, 8>(), 0, none},
+        {"k6t8-w256-bm512", one_kernel<6, 8, 2, 4, 8>(), 0, none},
+        {"k4t8-w256-bm256", one_kernel<4, 8, 2, 2, 8>(), 0, none},
+        {"k8t4-w512-bm1024", one_kernel<8, 4, 4, 16, 8>(), 0, none},
+        {"slots-k8t4-bm256", slot_kernel<8, 4, 8, 8>(), 0, none},
+        {"slots-k4t8-bm256", slot_kernel<4, 8, 8, 8>(), 0, none},
+        {"slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 0, none},
+        {"tall-k8t2-bm1024", tall_kernel<8, 2, 16, 16>(), 0, none},
+        {"tall-k8t2-bm1024-from256+slots-k4t8-bm256", slot_kernel<4, 8, 8, 8>(), 256, tall_kernel<8, 2, 16, 16>()},
+        {"tall-k8t2-bm1024-from256+slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 256, tall_kernel<8, 2, 16, 16>()},
+        {"tall-k8t2-bm1024-from512+slots-k4t8-bm256", slot_kernel<4, 8, 8, 8>(), 512, tall_kernel<8, 2, 16, 16>()},
+        {"tall-k8t2-bm1024-from512+slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 512, tall_kernel<8, 2, 16, 16>()},
     };
     return v;
 }
 
 // ------------------------------------------------------------------ planning
 
-// Tile descriptors of a variant, as bytes (BTile or PTile records).
-void build_tiles(const std::vector<BProd> &prods, const BVariant &v, std::vector<unsigned char> &bytes, int *ntiles)
+// Tile descriptors of one variant: list 0 for `main`, list 1 for `tall`
+// (empty unless split), as bytes of BTile or PTile records.
+struct TileLists {
+    std::vector<unsigned char> bytes[2];
+    int ntiles[2] = {0, 0};
+};
+
+// A slot unit: (product, row block, 128-column chunk).
+struct Unit { int prod, row0, word0, groups, rows; };
+
+// Slot units grouped 8 per tile among units with similar pass counts and
+// row counts; a tile's pad[0] is the largest row count of its slots.
+void pack_units(std::vector<Unit> &units, std::vector<unsigned char> &bytes, int *ntiles)
 {
-    bytes.clear();
-    *ntiles = 0;
-    if (!v.packed) {
-        std::vector<BTile> tiles;
-        const int tw = 2 * v.lpr;
-        for (size_t i = 0; i < prods.size(); ++i) {
-            const BProd &p = prods[i];
-            if (p.m <= 0 || p.n <= 0) continue;
-            const int64_t W = words_of(p.n);
-            for (int64_t r = 0; r < p.m; r += v.bm)
-                for (int64_t w = 0; w < W; w += tw) tiles.push_back(BTile{(int)i, (int)r, (int)w, 0});
-        }
-        // longest K first (the work of a tile grows with the K extent)
-        std::stable_sort(tiles.begin(), tiles.end(), [&](const BTile &a, const BTile &b) {
-            return prods[a.prod].l > prods[b.prod].l;
-        });
-        bytes.resize(tiles.size() * sizeof(BTile));
-        if (!tiles.empty()) memcpy(bytes.data(), tiles.data(), bytes.size());
-        *ntiles = (int)tiles.size();
-        return;
-    }
-    // slot units: (product, row block, 128-column chunk), grouped 8 per tile
-    // among units with similar pass counts and row counts
-    struct Unit { int prod, row0, word0, groups, rows; };
-    std::vector<Unit> units;
-    const int kg = v.k * v.t;
-    for (size_t i = 0; i < prods.size(); ++i) {
-        const BProd &p = prods[i];
-        if (p.m <= 0 || p.n <= 0) continue;
-        const int64_t W = words_of(p.n);
-        const int groups = (int)((p.l + kg - 1) / kg);
-        for (int64_t r = 0; r < p.m; r += v.bm)
-            for (int64_t w = 0; w < W; w += 2)
-                units.push_back(Unit{(int)i, (int)r, (int)w, groups, (int)std::min<int64_t>(v.bm, p.m - r)});
-    }
     std::stable_sort(units.begin(), units.end(), [](const Unit &a, const Unit &b) {
         return a.groups != b.groups ? a.groups > b.groups : a.rows > b.rows;
     });
@@ -448,6 +621,7 @@ void build_tiles(const std::vector<BProd> &prods, const BVariant &v, std::vector
             if (u < units.size()) {
                 T.slot[j] = PSlot{units[u].prod, units[u].row0, units[u].word0, 0};
                 T.groups = std::max(T.groups, units[u].groups);
+                T.pad[0] = std::max(T.pad[0], units[u].rows);
             } else {
                 T.slot[j] = PSlot{-1, 0, 0, 0};
             }
@@ -458,7 +632,61 @@ void build_tiles(const std::vector<BProd> &prods, const BVariant &v, std::vector
     *ntiles = (int)tiles.size();
 }
 
-int grid_for(const BVariant &v)
+// Units of rows [r_lo, m) of product i in row blocks of bm rows.
+void add_units(std::vector<Unit> &units, const BProd &p, int i, int64_t r_lo, int bm, int kg)
+{
+    const int64_t W = words_of(p.n);
+    const int groups = (int)((p.l + kg - 1) / kg);
+    for (int64_t r = r_lo; r < p.m; r += bm)
+        for (int64_t w = 0; w < W; w += 2)
+            units.push_back(Unit{i, (int)r, (int)w, groups, (int)std::min<int64_t>(bm, p.m - r)});
+}
+
+void build_tiles(const std::vector<BProd> &prods, const BVariant &v, TileLists &out)
+{
+    out = TileLists{};
+    const BKernel &k = v.main;
+    if (!k.packed) {
+        std::vector<BTile> tiles;
+        const int tw = 2 * k.lpr;
+        for (size_t i = 0; i < prods.size(); ++i) {
+            const BProd &p = prods[i];
+            if (p.m <= 0 || p.n <= 0) continue;
+            const int64_t W = words_of(p.n);
+            for (int64_t r = 0; r < p.m; r += k.bm)
+                for (int64_t w = 0; w < W; w += tw) tiles.push_back(BTile{(int)i, (int)r, (int)w, 0});
+        }
+        // longest K first (the work of a tile grows with the K extent)
+        std::stable_sort(tiles.begin(), tiles.end(), [&](const BTile &a, const BTile &b) {
+            return prods[a.prod].l > prods[b.prod].l;
+        });
+        out.bytes[0].resize(tiles.size() * sizeof(BTile));
+        if (!tiles.empty()) memcpy(out.bytes[0].data(), tiles.data(), out.bytes[0].size());
+        out.ntiles[0] = (int)tiles.size();
+        return;
+    }
+    std::vector<Unit> units, tall;
+    for (size_t i = 0; i < prods.size(); ++i) {
+        const BProd &p = prods[i];
+        if (p.m <= 0 || p.n <= 0) continue;
+        int64_t r_lo = 0;
+        if (v.split > 0) {
+            // rows [0, r_lo) on the tall kernel: its full blocks, and the last
+            // block too if it keeps `split` rows
+            const int64_t tb = v.tall.bm;
+            const int64_t full = p.m / tb * tb;
+            r_lo = p.m - full >= v.split ? p.m : full;
+            BProd q = p;
+            q.m = r_lo;
+            add_units(tall, q, (int)i, 0, (int)tb, v.tall.k * v.tall.t);
+        }
+        add_units(units, p, (int)i, r_lo, k.bm, k.k * k.t);
+    }
+    pack_units(units, out.bytes[0], &out.ntiles[0]);
+    if (v.split > 0) pack_units(tall, out.bytes[1], &out.ntiles[1]);
+}
+
+int grid_for(const BKernel &v)
 {
     int dev = 0, sms = 1, per = 1;
     cudaGetDevice(&dev);
@@ -492,10 +720,11 @@ std::string signature(const std::vector<BProd> &prods, int accumulate)
 struct GraphEntry {
     std::vector<unsigned long long> key;    // operand pointers, sizes, strides, stream, options
     int variant = -1;
-    void *dev = nullptr;                     // descriptor tables + counter (one cudaMalloc)
+    void *dev = nullptr;                     // descriptor tables + counters (one cudaMalloc)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    int ntiles = 0;
+    int ntiles = 0;                          // over both kernels
+    int nkernels = 0;                        // kernel nodes of the graph
 };
 std::mutex g_mu;
 std::list<GraphEntry> g_graphs;             // most recently used first
@@ -511,37 +740,69 @@ void free_entry(GraphEntry &e)
     e.dev = nullptr;
 }
 
-// Device copies of the tables: [prods][tiles][counter]
-int upload(const std::vector<BProd> &prods, const std::vector<unsigned char> &tiles, void **dev, BProd **dp,
-           void **dt, unsigned int **dc)
+// Device copies of the tables: [prods][tiles of main][tiles of tall][2 counters]
+struct DevTables {
+    void *dev = nullptr;
+    BProd *prods = nullptr;
+    void *tiles[2] = {nullptr, nullptr};
+    unsigned int *counters = nullptr;
+};
+
+int upload(const std::vector<BProd> &prods, const TileLists &tl, DevTables *d)
 {
     const size_t bp = (prods.size() * sizeof(BProd) + 255) & ~(size_t)255;
-    const size_t bt = (tiles.size() + 255) & ~(size_t)255;
+    const size_t bt0 = (tl.bytes[0].size() + 255) & ~(size_t)255;
+    const size_t bt1 = (tl.bytes[1].size() + 255) & ~(size_t)255;
     void *p = nullptr;
-    if (cudaMalloc(&p, bp + bt + 256) != cudaSuccess) {
+    if (cudaMalloc(&p, bp + bt0 + bt1 + 256) != cudaSuccess) {
         cudaGetLastError();
         return GF2_ENOMEM;
     }
     char *c = static_cast<char *>(p);
+    d->dev = p;
+    d->prods = reinterpret_cast<BProd *>(c);
+    d->tiles[0] = c + bp;
+    d->tiles[1] = c + bp + bt0;
+    d->counters = reinterpret_cast<unsigned int *>(c + bp + bt0 + bt1);
     GF2_CUDA_TRY(cudaMemcpy(c, prods.data(), prods.size() * sizeof(BProd), cudaMemcpyHostToDevice));
-    if (!tiles.empty())
-        GF2_CUDA_TRY(cudaMemcpy(c + bp, tiles.data(), tiles.size(), cudaMemcpyHostToDevice));
-    *dev = p;
-    *dp = reinterpret_cast<BProd *>(c);
-    *dt = c + bp;
-    *dc = reinterpret_cast<unsigned int *>(c + bp + bt);
+    for (int j = 0; j < 2; ++j)
+        if (!tl.bytes[j].empty())
+            GF2_CUDA_TRY(cudaMemcpy(d->tiles[j], tl.bytes[j].data(), tl.bytes[j].size(), cudaMemcpyHostToDevice));
     return GF2_OK;
 }
 
-int launch_variant(const BVariant &v, const BProd *dp, const void *dt, int ntiles, unsigned int *dc,
-                   int accumulate, cudaStream_t s)
+// The kernels of a variant in launch order (tall first: its tiles are the
+// longest), with their tile lists and counters.
+int kernels_of(const BVariant &v, const TileLists &tl, const DevTables &d, const BKernel *ks[2], const void *ts[2],
+               int nts[2], unsigned int *cs[2])
 {
-    GF2_CUDA_TRY(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
-    GF2_CUDA_TRY(cudaMemsetAsync(dc, 0, sizeof(unsigned int), s));
-    ProfScope ps(PF_BATCHED, s);
-    v.fn<<<grid_for(v), v.nw * 32, v.smem, s>>>(dp, dt, ntiles, dc, accumulate);
-    note_launch();
-    return check_launch();
+    int n = 0;
+    if (v.split > 0 && tl.ntiles[1] > 0) {
+        ks[n] = &v.tall; ts[n] = d.tiles[1]; nts[n] = tl.ntiles[1]; cs[n] = d.counters + 1; ++n;
+    }
+    if (tl.ntiles[0] > 0) {
+        ks[n] = &v.main; ts[n] = d.tiles[0]; nts[n] = tl.ntiles[0]; cs[n] = d.counters; ++n;
+    }
+    return n;
+}
+
+int launch_variant(const BVariant &v, const TileLists &tl, const DevTables &d, int accumulate, cudaStream_t s)
+{
+    const BKernel *ks[2];
+    const void *ts[2];
+    int nts[2];
+    unsigned int *cs[2];
+    const int nk = kernels_of(v, tl, d, ks, ts, nts, cs);
+    GF2_CUDA_TRY(cudaMemsetAsync(d.counters, 0, 2 * sizeof(unsigned int), s));
+    for (int j = 0; j < nk; ++j) {
+        GF2_CUDA_TRY(cudaFuncSetAttribute(ks[j]->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ks[j]->smem));
+        ProfScope ps(PF_BATCHED, s);
+        ks[j]->fn<<<grid_for(*ks[j]), ks[j]->nw * 32, ks[j]->smem, s>>>(d.prods, ts[j], nts[j], cs[j], accumulate);
+        note_launch();
+        const int rc = check_launch();
+        if (rc) return rc;
+    }
+    return GF2_OK;
 }
 
 int autotune_timed(const std::vector<BProd> &prods, int accumulate, cudaStream_t s);
@@ -610,26 +871,26 @@ int autotune_timed(const std::vector<BProd> &prods, int accumulate, cudaStream_t
     if (ev.create()) return GF2_ECUDA;
     cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     for (size_t i = 0; i < vs.size(); ++i) {
-        std::vector<unsigned char> tiles;
-        int nt = 0;
-        build_tiles(prods, vs[i], tiles, &nt);
-        void *dev = nullptr;
-        BProd *dp;
-        void *dt;
-        unsigned int *dc;
-        if (upload(prods, tiles, &dev, &dp, &dt, &dc)) continue;
+        TileLists tl;
+        build_tiles(prods, vs[i], tl);
+        DevTables d;
+        if (upload(prods, tl, &d)) {
+            if (d.dev) cudaFree(d.dev);
+            cudaGetLastError();
+            continue;
+        }
         float ms = 1e30f;
-        bool ok = launch_variant(vs[i], dp, dt, nt, dc, accumulate, s) == GF2_OK;
+        bool ok = launch_variant(vs[i], tl, d, accumulate, s) == GF2_OK;
         for (int rep = 0; ok && rep < 2; ++rep) {
             cudaEventRecord(e0, s);
-            ok = launch_variant(vs[i], dp, dt, nt, dc, accumulate, s) == GF2_OK;
+            ok = launch_variant(vs[i], tl, d, accumulate, s) == GF2_OK;
             cudaEventRecord(e1, s);
             float t = 0.f;
             if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
                 ms = std::min(ms, t);
         }
         cudaStreamSynchronize(s);
-        cudaFree(dev);
+        cudaFree(d.dev);
         cudaGetLastError();
         if (ok && ms < best_ms) {
             best_ms = ms;
@@ -689,7 +950,7 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
             if (g_graphs.front().ntiles == 0) return GF2_OK;
             ProfScope ps(PF_BATCHED, s);
             GF2_CUDA_TRY(cudaGraphLaunch(g_graphs.front().exec, s));
-            note_launch();
+            note_launch(g_graphs.front().nkernels);
             return GF2_OK;
         }
     }
@@ -715,45 +976,56 @@ int batched_mul(gf2_mat *const C[], const gf2_mat *const A[], const gf2_mat *con
     GraphEntry e;
     e.key = key;
     e.variant = vi;
-    std::vector<unsigned char> tiles;
-    int nt_built = 0;
-    build_tiles(prods, v, tiles, &nt_built);
-    e.ntiles = nt_built;
+    TileLists tl;
+    build_tiles(prods, v, tl);
+    e.ntiles = tl.ntiles[0] + tl.ntiles[1];
     if (e.ntiles > 0) {
-        BProd *dp;
-        void *dt;
-        unsigned int *dc;
-        int rc = upload(prods, tiles, &e.dev, &dp, &dt, &dc);
-        if (rc) return rc;
-        GF2_CUDA_TRY(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
-        // graph: reset the work counter, then the persistent kernel
+        DevTables d;
+        int rc = upload(prods, tl, &d);
+        e.dev = d.dev;
+        if (rc) { free_entry(e); return rc; }
+        const BKernel *ks[2];
+        const void *ts[2];
+        int nts[2];
+        unsigned int *cs[2];
+        const int nk = kernels_of(v, tl, d, ks, ts, nts, cs);
+        e.nkernels = nk;
+        // graph: reset the work counters, then the persistent kernels in order
         if (cudaGraphCreate(&e.graph, 0) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
-        cudaGraphNode_t nmem, nker;
+        cudaGraphNode_t prev;
         cudaMemsetParams mp;
         memset(&mp, 0, sizeof mp);
-        mp.dst = dc;
+        mp.dst = d.counters;
         mp.value = 0;
         mp.elementSize = sizeof(unsigned int);
-        mp.width = 1;
+        mp.width = 2;
         mp.height = 1;
-        mp.pitch = sizeof(unsigned int);
-        if (cudaGraphAddMemsetNode(&nmem, e.graph, nullptr, 0, &mp) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
-        int nt = e.ntiles;
-        void *args[5] = {(void *)&dp, (void *)&dt, (void *)&nt, (void *)&dc, (void *)&accumulate};
-        cudaKernelNodeParams kp;
-        memset(&kp, 0, sizeof kp);
-        kp.func = (void *)v.fn;
-        kp.gridDim = dim3((unsigned)grid_for(v));
-        kp.blockDim = dim3((unsigned)(v.nw * 32));
-        kp.sharedMemBytes = (unsigned)v.smem;
-        kp.kernelParams = args;
-        if (cudaGraphAddKernelNode(&nker, e.graph, &nmem, 1, &kp) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        mp.pitch = 2 * sizeof(unsigned int);
+        if (cudaGraphAddMemsetNode(&prev, e.graph, nullptr, 0, &mp) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+        for (int j = 0; j < nk; ++j) {
+            GF2_CUDA_TRY(cudaFuncSetAttribute(ks[j]->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ks[j]->smem));
+            const BProd *dp = d.prods;
+            const void *dt = ts[j];
+            int nt = nts[j];
+            unsigned int *dc = cs[j];
+            void *args[5] = {(void *)&dp, (void *)&dt, (void *)&nt, (void *)&dc, (void *)&accumulate};
+            cudaKernelNodeParams kp;
+            memset(&kp, 0, sizeof kp);
+            kp.func = (void *)ks[j]->fn;
+            kp.gridDim = dim3((unsigned)grid_for(*ks[j]));
+            kp.blockDim = dim3((unsigned)(ks[j]->nw * 32));
+            kp.sharedMemBytes = (unsigned)ks[j]->smem;
+            kp.kernelParams = args;
+            cudaGraphNode_t node;
+            if (cudaGraphAddKernelNode(&node, e.graph, &prev, 1, &kp) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
+            prev = node;
+        }
         if (cudaGraphInstantiate(&e.exec, e.graph, 0) != cudaSuccess) { free_entry(e); cudaGetLastError(); return GF2_ECUDA; }
         {
             ProfScope ps(PF_BATCHED, s);
             if (cudaGraphLaunch(e.exec, s) != cudaSuccess) { free_entry(e); return GF2_ECUDA; }
         }
-        note_launch();
+        note_launch(nk);
     }
     g_graphs.push_front(std::move(e));
     while (g_graphs.size() > kMaxGraphs) {

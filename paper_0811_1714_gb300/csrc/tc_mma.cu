@@ -34,9 +34,13 @@
 //    values into parity words of C in registers.  No bit expansion competes
 //    with the tensor core.  PAIR = 1: clusters of two CTAs over 256 x 256
 //    tiles with one tcgen05.mma.cta_group::2 stream (M = 256), two K blocks
-//    per stage; PAIR = 0: one CTA per 128 x TN tile.  FP8 double-buffers its
-//    accumulator; FP4's scale factors fill columns 256-287 and 320-351, which
-//    leaves room for one 256-column accumulator.
+//    per stage; PAIR = 0: one CTA per 128 x TN tile.  Accumulators are
+//    double-buffered (the MMAs of the next tile run while the epilogue reads
+//    the last one) except on single-CTA FP4 256-column tiles: FP8 pairs take
+//    256-column tiles (accumulators at columns 0 and 256 of tensor memory),
+//    FP4 pairs 224-column tiles (accumulators at 0 and 256, the scale factors
+//    in the 32 columns after each), whose ends fall on 32-bit boundaries of
+//    C's words.
 //  - the batched form (many products of uneven shapes): expand_batched_kernel
 //    (A rows) and expand_t_batched_kernel (B^T rows straight from packed B,
 //    transposed by ballots in shared-memory-staged 64 x 512-entry units), then
@@ -70,7 +74,18 @@ constexpr int A_BYTES = BM * ROWB;            // 16 KB
 constexpr int TMA_WARP = 0, MMA_WARP = 1, EPI_WARP0 = 2, NUM_EPI_WARPS = 8;
 constexpr int NTHREADS = (EPI_WARP0 + NUM_EPI_WARPS) * 32;    // 320
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t SFA_COL = 256, SFB_COL = 320;  // FP4 scale factors (32 columns each)
+constexpr int PTN_F4 = 224;                   // tile columns of the FP4 pairs (two accumulators)
+
+// Tensor-memory columns of a tile width: accumulator b at b * ACC, FP4 scale
+// factors (32 columns each, every byte 1.0) at SFA and SFB.  256-column tiles
+// hold one FP4 accumulator (scale factors at 256 and 320); 224-column tiles
+// two (at 0 and 256, scale factors in the 32 columns after each); 128-column
+// tiles two (at 0 and 128).
+template <int TN> struct Cols {
+    static constexpr uint32_t ACC = TN == 224 ? 256 : TN;
+    static constexpr uint32_t SFA = TN == 224 ? 224 : 256;
+    static constexpr uint32_t SFB = TN == 224 ? 480 : 320;
+};
 
 // Per-CTA stage and ring: KBS 128-byte K blocks per stage; per block one CTA
 // holds its A tile and the whole B^T tile (48 KB), each CTA of a pair its A
@@ -98,8 +113,8 @@ template <> struct Fmt<KIND_F8> {
 };
 template <> struct Fmt<KIND_F4> {
     static constexpr int EPR = 256;
-    // the scale factors take columns 256-351, so 256-column tiles have one
-    // accumulator and 128-column tiles two
+    // with the scale factors beside them, 256-column tiles have room for one
+    // accumulator, 224- and 128-column tiles for two
     static constexpr int nacc(int TN) { return TN == 256 ? 1 : 2; }
     // one accumulator: every chunk boundary idles the tensor core while the
     // epilogue reads it out, so the chunks are twice as long (sums <= 2^13)
@@ -125,7 +140,7 @@ struct alignas(128) TcxProd {
 struct Params {
     int64_t m, n;            // rows of A (and of C), rows of B^T (columns of C) per product
     int64_t nkb;             // 128-byte K blocks per row
-    int tiles_m, tiles_n;    // tile rows of 128 (one CTA) or 256 (a pair) rows, tile columns of 256
+    int tiles_m, tiles_n;    // tile rows of 128 (one CTA) or 256 (a pair) rows, tile columns of TN
     int batch;
     uint64_t *C;
     int64_t ldc, bsC;
@@ -170,12 +185,14 @@ __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t ad, uint64_t bd, 
         if (PAIR)
             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
                          "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
-                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + SFA_COL), "r"(tmem_base + SFB_COL), "r"(acc)
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + Cols<TN>::SFA),
+                           "r"(tmem_base + Cols<TN>::SFB), "r"(acc)
                          : "memory");
         else
             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
                          "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
-                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + SFA_COL), "r"(tmem_base + SFB_COL), "r"(acc)
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + Cols<TN>::SFA),
+                           "r"(tmem_base + Cols<TN>::SFB), "r"(acc)
                          : "memory");
     }
 }
@@ -292,11 +309,13 @@ template <int KIND, int PAIR, int TN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Params P)
 {
-    static_assert(TN == 256 || (TN == 128 && !PAIR), "tile widths: 256, or 128 on one CTA");
+    static_assert(TN == 256 || (TN == 224 && PAIR) || (TN == 128 && !PAIR),
+                  "tile widths: 256, 224 on pairs, 128 on one CTA");
     constexpr int KBS = PAIR ? KBS_PAIR : KBS_ONE;
     using R = Ring<PAIR, KBS, TN>;
     constexpr int NACC = Fmt<KIND>::nacc(TN);
-    constexpr int NL = TN / 64;                 // 32-column loads of an epilogue warp (its TN / 2 columns)
+    constexpr int G = TN / 32;                  // 32-column groups of a tile
+    constexpr int GH = (G + 1) / 2;             // groups of the first epilogue column half
     constexpr int SPC = Fmt<KIND>::KCHUNK / Fmt<KIND>::EPR / KBS;   // stages per K-chunk
     constexpr int STAGES = R::STAGES;
     constexpr int STAGE_BYTES = R::STAGE_BYTES;
@@ -342,8 +361,8 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         // every scale factor 1.0 (UE8M0 127): whatever bytes of these columns
         // the MMA reads for A and for B, each block product is unscaled
         const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-        tmem_fill32(tmem_base + lanes + SFA_COL, 0x7F7F7F7Fu);
-        tmem_fill32(tmem_base + lanes + SFB_COL, 0x7F7F7F7Fu);
+        tmem_fill32(tmem_base + lanes + Cols<TN>::SFA, 0x7F7F7F7Fu);
+        tmem_fill32(tmem_base + lanes + Cols<TN>::SFB, 0x7F7F7F7Fu);
         tmem_wait_st();
     }
     fence_before();
@@ -442,7 +461,7 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                         break;
                     }
                     fence_after();
-                    const uint32_t dt = tmem_base + (uint32_t)(ab * TN);
+                    const uint32_t dt = tmem_base + (uint32_t)ab * Cols<TN>::ACC;
                     const int64_t ks0 = (int64_t)c * SPC;
                     const int64_t ks1 = std::min<int64_t>(nst, ks0 + SPC);
                     for (int64_t ks = ks0; ks < ks1; ++ks, ++it) {
@@ -474,7 +493,8 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     } else {
         // ------------------------------------------------------------ epilogue
         const int quarter = warp & 3;                   // TMEM lanes 32*quarter.. = tile rows
-        const int half = (warp - EPI_WARP0) >> 2;       // columns (TN / 2) * half ..
+        const int half = (warp - EPI_WARP0) >> 2;       // column groups GH * half ..
+        const int ng = half == 0 ? GH : G - GH;         // this warp's 32-column groups
         const int row_in_tile = (int)rank * BM + quarter * 32 + lane;
         uint32_t u = 0;
         for (int64_t t = t0; t < tiles && !warp_aborted(abort_flag); t += tstep) {
@@ -483,9 +503,9 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const int64_t nst = (T.nkb + KBS - 1) / KBS;
             const int nchunks = (int)((nst + SPC - 1) / SPC);
             const int64_t nW = words_of(T.n);
-            uint32_t par[NL];
+            uint32_t par[GH];
 #pragma unroll
-            for (int g = 0; g < NL; ++g) par[g] = 0u;
+            for (int g = 0; g < GH; ++g) par[g] = 0u;
             bool ok = true;
             for (int c = 0; c < nchunks; ++c, ++u) {
                 const int ab = (int)(u % NACC);
@@ -494,11 +514,12 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     break;
                 }
                 fence_after();
-                const uint32_t taddr =
-                    tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * TN + half * (TN / 2));
-                uint32_t r[32 * NL];
+                const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                                       (uint32_t)ab * Cols<TN>::ACC + (uint32_t)(half * GH * 32);
+                uint32_t r[32 * GH];
 #pragma unroll
-                for (int g = 0; g < NL; ++g) tmem_ld32(taddr + 32 * g, r + 32 * g);
+                for (int g = 0; g < GH; ++g)
+                    if (g < ng) tmem_ld32(taddr + 32 * g, r + 32 * g);
                 tmem_wait_ld();
                 // the accumulator is in registers: hand it back to the MMA
                 fence_before();
@@ -508,7 +529,8 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     else mbar_arrive(tempty_bar(ab));
                 }
 #pragma unroll
-                for (int g = 0; g < NL; ++g) {
+                for (int g = 0; g < GH; ++g) {
+                    if (g >= ng) break;
                     uint32_t word = 0;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -523,12 +545,28 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             const int64_t grow = (int64_t)tm * TILE_ROWS + row_in_tile;
             if (grow < T.m) {
                 uint64_t *C = T.C + grow * T.ldc;
+                if constexpr (TN % 64 == 0) {
+                    // whole 64-bit words of C per column half
 #pragma unroll
-                for (int i = 0; i < NL / 2; ++i) {
-                    const int64_t wcol = (int64_t)tn * (TN / 64) + half * (NL / 2) + i;
-                    if (wcol < nW) {
-                        const uint64_t v = (((uint64_t)par[2 * i + 1] << 32) | par[2 * i]) & word_mask(wcol, T.n);
-                        C[wcol] = P.accumulate ? (C[wcol] ^ v) : v;
+                    for (int i = 0; i < GH / 2; ++i) {
+                        const int64_t wcol = (int64_t)tn * (TN / 64) + half * (GH / 2) + i;
+                        if (wcol < nW) {
+                            const uint64_t v = (((uint64_t)par[2 * i + 1] << 32) | par[2 * i]) & word_mask(wcol, T.n);
+                            C[wcol] = P.accumulate ? (C[wcol] ^ v) : v;
+                        }
+                    }
+                } else {
+                    // 224-column tiles end on 32-bit boundaries: 32-bit words of
+                    // C (the low and high halves of its little-endian 64-bit
+                    // words), each owned by one tile
+                    uint32_t *C32 = reinterpret_cast<uint32_t *>(C);
+#pragma unroll
+                    for (int g = 0; g < GH; ++g) {
+                        const int64_t w32 = (int64_t)tn * G + half * GH + g;
+                        if (g < ng && w32 < 2 * nW) {
+                            const uint32_t v = par[g] & (uint32_t)(word_mask(w32 >> 1, T.n) >> (32 * (w32 & 1)));
+                            C32[w32] = P.accumulate ? (C32[w32] ^ v) : v;
+                        }
                     }
                 }
             }
@@ -731,15 +769,15 @@ bool pairs_disabled()
     return e && e[0] == '0';
 }
 
-template <int KIND, int PAIR>
+template <int KIND, int PAIR, int TN>
 int mma_launch_v(const CUtensorMap &mapA, const CUtensorMap &mapB, const Params &P, int sms, cudaStream_t s)
 {
-    constexpr int SMEM = Ring<PAIR, PAIR ? KBS_PAIR : KBS_ONE, BN>::SMEM_BYTES;
+    constexpr int SMEM = Ring<PAIR, PAIR ? KBS_PAIR : KBS_ONE, TN>::SMEM_BYTES;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     static int max_clusters = 0;
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(tc_mma_kernel<KIND, PAIR, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        attr_err = cudaFuncSetAttribute(tc_mma_kernel<KIND, PAIR, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (attr_err == cudaSuccess && PAIR) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute at[1];
@@ -752,7 +790,7 @@ int mma_launch_v(const CUtensorMap &mapA, const CUtensorMap &mapB, const Params 
             cfg.dynamicSmemBytes = SMEM;
             cfg.attrs = at;
             cfg.numAttrs = 1;
-            if (cudaOccupancyMaxActiveClusters(&max_clusters, tc_mma_kernel<KIND, PAIR, BN>, &cfg) != cudaSuccess) {
+            if (cudaOccupancyMaxActiveClusters(&max_clusters, tc_mma_kernel<KIND, PAIR, TN>, &cfg) != cudaSuccess) {
                 cudaGetLastError();
                 max_clusters = 0;
             }
@@ -764,7 +802,7 @@ int mma_launch_v(const CUtensorMap &mapA, const CUtensorMap &mapB, const Params 
     ProfScope ps(KIND == KIND_F8 ? PF_TC : PF_TC_F4, s);
     if (!PAIR) {
         const int64_t grid = tiles < sms ? tiles : sms;
-        tc_mma_kernel<KIND, PAIR, BN><<<(unsigned)grid, NTHREADS, SMEM, s>>>(mapA, mapB, P);
+        tc_mma_kernel<KIND, PAIR, TN><<<(unsigned)grid, NTHREADS, SMEM, s>>>(mapA, mapB, P);
     } else {
         const int64_t clusters = std::min<int64_t>(tiles, max_clusters);
         cudaLaunchConfig_t cfg = {};
@@ -779,7 +817,7 @@ int mma_launch_v(const CUtensorMap &mapA, const CUtensorMap &mapB, const Params 
         cfg.stream = s;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        GF2_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_mma_kernel<KIND, PAIR, BN>, mapA, mapB, P));
+        GF2_CUDA_TRY(cudaLaunchKernelEx(&cfg, tc_mma_kernel<KIND, PAIR, TN>, mapA, mapB, P));
     }
     note_launch();
     return check_launch();
@@ -794,11 +832,14 @@ int mma_launch(const TcxLaunch &L, cudaStream_t s)
     // pairs of CTAs on 256-row tiles wherever there are at least two 128-row
     // tile rows; single CTAs otherwise (or with GF2_TC_PAIRS=0)
     const bool pair = L.m > BM && !pairs_disabled();
+    // FP4 pairs take 224-column tiles, whose two accumulators and scale
+    // factors fit the 512 columns of tensor memory; everything else 256
+    constexpr int PTN = KIND == KIND_F4 ? PTN_F4 : BN;
     Params P;
     P.m = L.m; P.n = L.n;
     P.nkb = L.rowbytes / ROWB;
     P.tiles_m = div_up(L.m, pair ? 2 * BM : BM);
-    P.tiles_n = div_up(L.n, BN);
+    P.tiles_n = div_up(L.n, pair ? PTN : BN);
     P.batch = L.batch;
     P.C = L.C; P.ldc = L.ldc; P.bsC = L.bsC;
     P.accumulate = L.accumulate;
@@ -810,14 +851,17 @@ int mma_launch(const TcxLaunch &L, cudaStream_t s)
     CUtensorMap mapA, mapB;
     int rc = make_map(&mapA, L.XA, L.rowbytes, L.m, L.batch, BM);
     if (rc) return rc;
-    rc = make_map(&mapB, L.XB, L.rowbytes, L.n, L.batch, BN / 2);     // B^T tiles as 128-row halves
-    if (rc) return rc;
     if (pair) {
-        rc = mma_launch_v<KIND, 1>(mapA, mapB, P, sms, s);
+        rc = make_map(&mapB, L.XB, L.rowbytes, L.n, L.batch, PTN / 2);   // each CTA's half of a B^T tile
+        if (rc) return rc;
+        rc = mma_launch_v<KIND, 1, PTN>(mapA, mapB, P, sms, s);
         if (rc != GF2_EUNSUPPORTED) return rc;
         P.tiles_m = div_up(L.m, BM);
+        P.tiles_n = div_up(L.n, BN);
     }
-    return mma_launch_v<KIND, 0>(mapA, mapB, P, sms, s);
+    rc = make_map(&mapB, L.XB, L.rowbytes, L.n, L.batch, BN / 2);     // B^T tiles as 128-row halves
+    if (rc) return rc;
+    return mma_launch_v<KIND, 0, BN>(mapA, mapB, P, sms, s);
 }
 
 // ------------------------------------------------------------------ batched form

@@ -133,3 +133,20 @@ def test_clock_summary_keeps_the_timed_region():
     assert s["reasons"] == ["sw_power_cap"]
     whole = cs.summary()
     assert whole["samples"] == 6 and "hw_slowdown" in whole["reasons"]
+
+
+def test_batched_table_bytes_follow_each_row_block_k():
+    """m*l*n/(8k) per product; split variants count the tall row blocks
+    (full 1024-row blocks, and the last one when it keeps the threshold's
+    rows) at k = 8 and the rest at the slot kernel's k."""
+    dims = [(1100, 64, 128), (1300, 64, 128), (200, 64, 128)]
+    b, _ = bench.batched_table_bytes("slots-k4t8-bm256", dims)
+    assert b == pytest.approx(sum(m * l * n for m, l, n in dims) / 32.0)
+    b, _ = bench.batched_table_bytes("tall-k8t2-bm1024-from256+slots-k4t8-bm128", dims)
+    # 1100: 1024 tall + 76 rest; 1300: all tall (276 >= 256); 200: all rest
+    want = (1024 * 64 * 128 / 64 + 76 * 64 * 128 / 32 + 1300 * 64 * 128 / 64 + 200 * 64 * 128 / 32)
+    assert b == pytest.approx(want)
+    b, _ = bench.batched_table_bytes("tall-k8t2-bm1024-from512+slots-k4t8-bm256", dims)
+    want = (1024 * 64 * 128 / 64 + 76 * 64 * 128 / 32 + 1024 * 64 * 128 / 64 + 276 * 64 * 128 / 32
+            + 200 * 64 * 128 / 32)
+    assert b == pytest.approx(want)

@@ -173,3 +173,12 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(g, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(g.LibraryNotBuilt):
         g.lib()
+
+
+def test_build_makes_the_peak_probe_program(lib):
+    """build() also compiles the throughput probes behind the roofline peaks
+    into an executable beside the library (run only by the GPU tests and
+    `bench.py --workload peaks`)."""
+    from paper_0811_1714_gb300 import buildlib
+    exe = buildlib.probe_path("peaks")
+    assert os.path.isfile(exe) and os.access(exe, os.X_OK)

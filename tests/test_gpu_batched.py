@@ -47,11 +47,14 @@ def make_batch(dims, seed0):
     return dict(hostA=hostA, hostB=hostB, dA=dA, dB=dB, dC=dC, arrs=g.MatArrays(MC, MA, MB))
 
 
+# includes row counts past one 1024-row tall block with remainders below,
+# between and above the split thresholds (76, 276, 600 rows)
 RAGGED = [(1, 1, 1), (64, 64, 64), (65, 63, 129), (300, 700, 100), (1000, 90, 1030),
-          (17, 2048, 5), (513, 257, 511), (2048, 300, 2048), (129, 1, 300), (7, 4000, 260)]
+          (17, 2048, 5), (513, 257, 511), (2048, 300, 2048), (129, 1, 300), (7, 4000, 260),
+          (1100, 200, 300), (1300, 65, 700), (1624, 33, 130)]
 
 
-NVARIANTS = 11   # 8 one-product-per-tile variants + 3 slot-packed variants
+NVARIANTS = 16   # 8 one-product-per-tile, 3 slot-packed, 1 tall slot-packed, 4 split variants
 
 
 @pytest.mark.parametrize("variant", list(range(NVARIANTS)))
@@ -64,6 +67,31 @@ def test_every_batched_variant(variant):
     for i, (m, l, n) in enumerate(RAGGED):
         ref = oracle.mul_packed(bt["hostA"][i], bt["hostB"][i], m, l, n)
         assert_same_bits(to_host(bt["dC"][i]), ref, n, "%s %s" % (g.gf2_batched_variant_name(variant), (m, l, n)))
+
+
+@pytest.fixture(scope="module")
+def ragged_refs():
+    bt = make_batch(RAGGED, 500)
+    refs = [oracle.mul_packed(bt["hostA"][i], bt["hostB"][i], m, l, n) for i, (m, l, n) in enumerate(RAGGED)]
+    return refs
+
+
+@pytest.mark.parametrize("variant", list(range(NVARIANTS)))
+def test_every_batched_variant_accumulates(variant, ragged_refs):
+    """C ^= A B through every variant's XOR epilogue (C0 random)."""
+    bt = make_batch(RAGGED, 500)
+    C0 = []
+    for i, (m, l, n) in enumerate(RAGGED):
+        c0 = synth.random_packed(m, n, 9100 + i)
+        bt["dC"][i].copy_(to_dev(c0))
+        C0.append(c0)
+    o = g.opts(base=g.GF2_BASE_M4RM, depth=0, accumulate=1)
+    used = g.gf2_mul_batched_ex(bt["arrs"], options=o, variant=variant)
+    assert used == variant
+    torch.cuda.synchronize()
+    for i, (m, l, n) in enumerate(RAGGED):
+        assert_same_bits(to_host(bt["dC"][i]), ragged_refs[i] ^ C0[i], n,
+                         "%s accumulate %s" % (g.gf2_batched_variant_name(variant), (m, l, n)))
 
 
 def test_autotuned_batch_and_graph_replay():

@@ -130,3 +130,22 @@ def test_tc_single_cta_tiles(m, l, n, base, monkeypatch):
     B = synth.random_packed(l, n, 32)
     ref = oracle.mul_packed(A, B, m, l, n)
     assert_same_bits(tc_mul(A, B, m, l, n, base=base), ref, n, "single-CTA tc %d %s" % (base, (m, l, n)))
+
+
+@pytest.mark.parametrize("n", [32, 96, 223, 224, 225, 447, 448, 449, 673, 1000, 2240])
+@pytest.mark.parametrize("accumulate", [0, 1])
+def test_fp4_pair_tile_columns(n, accumulate):
+    """FP4 pairs run 224-column tiles (two accumulators beside the scale
+    factors), which end on 32-bit boundaries of C's words: widths around the
+    tile width and its multiples, with and without C ^= A B, and bits past
+    the last column of the last word written as zero (or kept, with
+    accumulate)."""
+    m, l = 300, 1100
+    A = synth.random_packed(m, l, 41)
+    B = synth.random_packed(l, n, 42)
+    ref = oracle.mul_packed(A, B, m, l, n)
+    C0 = synth.random_packed(m, n, 43) if accumulate else None
+    if accumulate:
+        ref = ref ^ C0
+    got = tc_mul(A, B, m, l, n, accumulate=accumulate, C0=C0, base=g.GF2_BASE_TC_FP4)
+    assert_same_bits(got, ref, n, "fp4 pair n=%d acc=%d" % (n, accumulate))
