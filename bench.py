@@ -688,20 +688,22 @@ def run_reference(args):
 
 def batched_table_bytes(vname, dims):
     """Algorithmic table-row reads of a batched variant: m*l*n / (8k) bytes
-    per product for k-bit tables.  A split variant "tall-k8t2-bm1024-from<r>+
-    slots-k<k>t<t>-..." runs each product's full 1024-row blocks, and its last
+    per product for k-bit tables.  A split variant "tall-k8t4-bm<b>-from<r>+
+    slots-k<k>t<t>-..." runs each product's full b-row blocks, and its last
     block when that keeps at least r rows, with k = 8 and the other rows with
     the slot kernel's k."""
     import re
     if "+" in vname:
+        tb = int(re.search(r"^tall-k\d+t\d+-bm(\d+)-from", vname).group(1))
         split = int(re.search(r"-from(\d+)\+", vname).group(1))
         k_rest = int(re.search(r"\+slots-k(\d+)t", vname).group(1))
         total = 0.0
         for m, l, n in dims:
-            full = m // 1024 * 1024
+            full = m // tb * tb
             tall = m if m - full >= split else full
             total += tall * l * n / 64.0 + (m - tall) * l * n / (8.0 * k_rest)
-        return total, "k=8 on the tall row blocks (from %d rows), k=%d on the rest" % (split, k_rest)
+        return total, "k=8 on the tall row blocks (%d-row blocks, the last one from %d rows), k=%d on the rest" % (
+            tb, split, k_rest)
     k = int(re.search(r"k(\d+)t", vname).group(1))
     return sum(m * l * n for m, l, n in dims) / (8.0 * k), "k=%d tables" % k
 

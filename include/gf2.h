@@ -194,8 +194,8 @@ int32_t gf2_batched_variant_count(void);
 /* Name of one batched tile variant (NULL beyond the last), with k and t as
  * in Sections 3.1 and 3.3: "k<k>t<t>-w<columns>-bm<rows>" (one product per
  * tile), "slots-k<k>t<t>-bm<rows>" (8 products' 128-column slices per tile),
- * "tall-k8t2-bm1024" (slot tiles of 1024 rows), and
- * "tall-k8t2-bm1024-from<r>+slots-..." (row blocks of at least r rows on the
+ * "tall-k8t4-bm512" (slot tiles of 512 rows), and
+ * "tall-k8t4-bm512-from<r>+slots-..." (row blocks of at least r rows on the
  * tall kernel, the rest on the slot kernel). */
 const char *gf2_batched_variant_name(int32_t variant);
 

@@ -353,18 +353,19 @@ __global__ void __launch_bounds__(NW * 32) m4rm_slots_kernel(const BProd *__rest
     }
 }
 
-// Tall slot-packed tiles for k = 8 tables (Section 3.1; t tables per pass,
-// Section 3.3): the same 8 slots of 128 columns as m4rm_slots_kernel, but
-// 1024 rows per tile, so that one build of the 256-entry tables serves
-// four times as many lookups as a 256-row tile.  With t = 2 the tables take
-// 64 KB.  A is staged in 16-byte chunks per (row, slot) (128 entries of K,
-// 128 / (k t) passes) with coalescing-free 16-byte copies that bypass L1,
-// into ONE 128 KB buffer: the next chunk is copied after every warp's last
-// lookup in the current one, while the next pass builds its tables.  Each
-// thread stages one slot's rows (its slot is fixed by the thread index).
-// The tile's `rows` field is the largest row count of its slots: warps whose
-// rows all lie beyond it skip the lookups, so a tile of short row blocks
-// pays for the table build only.
+// Tall slot-packed tiles for k = 8 tables (Section 3.1; t = 4 tables per
+// pass, Section 3.3): the same 8 slots of 128 columns as m4rm_slots_kernel,
+// but 512 rows per tile (8 rows per thread), so that one build of the four
+// 256-entry tables (128 KB) serves four times as many lookups as a 128-row
+// tile.  A is staged in 16-byte chunks per (row, slot) (128 entries of K,
+// four passes) by 16-byte copies that bypass L1, into one 64 KB buffer; at
+// the start of a chunk every thread moves its rows' chunks into registers,
+// and once every thread has done so (the barrier before the lookups) the
+// next chunk is copied into the buffer, so it lands during the next four
+// passes and no lookup waits on a shared-memory read of A.  Each thread
+// stages one slot's rows (its slot is fixed by the thread index).  The
+// tile's `rows` field is the largest row count of its slots: warps whose
+// rows all lie beyond it skip the lookups.
 template <int KB, int NT, int R, int NW>
 __global__ void __launch_bounds__(NW * 32, 1) m4rm_tall_slots_kernel(const BProd *__restrict__ prods,
                                                                       const void *__restrict__ tiles_v,
@@ -375,11 +376,10 @@ __global__ void __launch_bounds__(NW * 32, 1) m4rm_tall_slots_kernel(const BProd
     constexpr int NTH = NW * 32;
     constexpr int KG = KB * NT;
     constexpr int TROWS = 1 << KB;
-    constexpr int BM = NW * 4 * R;
     constexpr int PPC = 128 / KG;                         // passes per staged 16-byte A chunk
     constexpr int SROWS = NTH / LPR;                      // rows one staging sweep covers
     constexpr unsigned IMASK = (1u << KB) - 1u;
-    static_assert(128 % KG == 0 && KG <= 32, "passes tile the 16-byte A chunks");
+    static_assert(128 % KG == 0 && KG == 32, "32-bit passes tile the 16-byte A chunks");
     static_assert(NTH % LPR == 0 && KG * LPR <= NTH, "");
     const PTile *tiles = static_cast<const PTile *>(tiles_v);
 
@@ -416,16 +416,22 @@ __global__ void __launch_bounds__(NW * 32, 1) m4rm_tall_slots_kernel(const BProd
         const uint64_t cm0 = mine ? word_mask(my_w, my_n) : 0ull, cm1 = mine ? word_mask(my_w + 1, my_n) : 0ull;
         const uint4 cmask = make_uint4((uint32_t)cm0, (uint32_t)(cm0 >> 32), (uint32_t)cm1, (uint32_t)(cm1 >> 32));
         const bool active = warp * 4 * R < rows;          // warp-uniform
-        // the staging thread's slot: its A rows srow + SROWS j below the slot's m
+        // the staging thread's slot: its A rows srow + SROWS j of the slot's
+        // row block (below the product's m and below `rows`, at most the
+        // tile's 4 R NW rows: the buffer holds no more)
         const bool s_mine = ss[cs].prod >= 0;
         const int64_t s_lda = s_mine ? sp[cs].lda : 0;
         const uint64_t *s_a = s_mine ? sp[cs].A + ((int64_t)ss[cs].row0 + srow) * s_lda : prods[0].A;
-        const int64_t s_left = s_mine ? sp[cs].m - ss[cs].row0 - srow : 0;
+        const int64_t s_end = s_mine ? sp[cs].m - ss[cs].row0 : 0;       // rows of the product from row0
+        const int64_t s_left = (s_end < rows ? s_end : rows) - srow;
         const int s_nj = s_left <= 0 ? 0 : (int)((s_left + SROWS - 1) / SROWS);
         const int64_t s_lw = s_mine ? words_of(sp[cs].l) : 0;
-        uint4 acc[R];
+        uint4 acc[R], areg[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = make_uint4(0, 0, 0, 0);
+        for (int r = 0; r < R; ++r) {
+            acc[r] = make_uint4(0, 0, 0, 0);
+            areg[r] = make_uint4(0, 0, 0, 0);
+        }
 
         auto issue_b = [&](int g, int buf) {
             if (tid < KG * LPR) {
@@ -444,7 +450,6 @@ __global__ void __launch_bounds__(NW * 32, 1) m4rm_tall_slots_kernel(const BProd
 #pragma unroll 1
             for (int j = 0; j < s_nj; ++j) {
                 const int row = srow + SROWS * j;
-                if (row >= rows) break;
                 cp_async16(&sta[row * LPR + cs], kin ? s_a + SROWS * j * s_lda + wa : prods[0].A, kin);
             }
         };
@@ -457,35 +462,36 @@ __global__ void __launch_bounds__(NW * 32, 1) m4rm_tall_slots_kernel(const BProd
 #pragma unroll 1
         for (int g = 0; g < groups; ++g) {
             const int buf = g & 1;
-            const bool new_chunk = g > 0 && (g % PPC) == 0;
+            const bool chunk_start = (g % PPC) == 0;
             cp_async_wait_all();
-            __syncthreads();                              // every warp is done with pass g - 1
-            if (new_chunk) issue_a(g / PPC);
+            __syncthreads();                              // B rows of pass g (and A chunk) landed
+            if (chunk_start && active) {
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (warp * 4 * R + 4 * r < rows) areg[r] = sta[(trow + 4 * r) * LPR + c];
+            }
             if (g + 1 < groups) issue_b(g + 1, buf ^ 1);
-            cp_async_commit();
             build_tables<KB, NT, NTH, LPR>(tab, stg + buf * KG * LPR, tid, cmask);
-            if (new_chunk) cp_async_wait_all();           // this pass's A chunk (and the next B rows)
-            __syncthreads();
+            __syncthreads();                              // tables built, A chunk in registers
+            if (chunk_start && g + PPC < groups) issue_a(g / PPC + 1);
+            cp_async_commit();
             if (active) {
                 const int64_t kb = (int64_t)g * KG;
-                const int sh = (int)(kb & 63);
-                const uint64_t mlo = mine ? word_mask(kb >> 6, my_l) : 0ull;
-                const int half = (g / (64 / KG)) & 1;    // 64-bit word of the chunk
-                const uint4 *arow = sta + trow * LPR + c;
+                const int q = g % PPC;                    // 32-bit word of the chunk
+                const uint32_t mlo = mine ? (uint32_t)(word_mask(kb >> 6, my_l) >> (kb & 63)) : 0u;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if (warp * 4 * R + 4 * r < rows) {
-                        const uint2 aw = reinterpret_cast<const uint2 *>(&arow[4 * r * LPR])[half];
-                        const uint64_t bits = ((((uint64_t)aw.y << 32) | aw.x) & mlo) >> sh;
+                        const uint32_t w = q == 0 ? areg[r].x : q == 1 ? areg[r].y : q == 2 ? areg[r].z : areg[r].w;
+                        const uint32_t bits = w & mlo;
                         uint4 a = acc[r];
 #pragma unroll
                         for (int ti = 0; ti < NT; ++ti) {
-                            const unsigned x = (unsigned)(bits >> (ti * KB)) & IMASK;
+                            const unsigned x = (bits >> (ti * KB)) & IMASK;
                             a = x4(a, tab[(ti * TROWS + (int)x) * LPR + c]);
                         }
                         acc[r] = a;
                     }
-                    asm volatile("" ::: "memory");
                 }
             }
         }
@@ -508,8 +514,8 @@ __global__ void __launch_bounds__(NW * 32, 1) m4rm_tall_slots_kernel(const BProd
                     if (4 * r >= nrows) break;
                     uint4 a = make_uint4(0, 0, 0, 0);
 #pragma unroll
-                    for (int q = 0; q < R; ++q)
-                        if (q == r) a = acc[q];
+                    for (int qq = 0; qq < R; ++qq)
+                        if (qq == r) a = acc[qq];
                     const uint64_t v0 = ((uint64_t)a.y << 32 | a.x) & cm0;
                     const uint64_t v1 = ((uint64_t)a.w << 32 | a.z) & cm1;
                     uint64_t *cc = cr + r * step;
@@ -584,11 +590,11 @@ const std::vector<BVariant> &bvariants()
         {"slots-k8t4-bm256", slot_kernel<8, 4, 8, 8>(), 0, none},
         {"slots-k4t8-bm256", slot_kernel<4, 8, 8, 8>(), 0, none},
         {"slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 0, none},
-        {"tall-k8t2-bm1024", tall_kernel<8, 2, 16, 16>(), 0, none},
-        {"tall-k8t2-bm1024-from256+slots-k4t8-bm256", slot_kernel<4, 8, 8, 8>(), 256, tall_kernel<8, 2, 16, 16>()},
-        {"tall-k8t2-bm1024-from256+slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 256, tall_kernel<8, 2, 16, 16>()},
-        {"tall-k8t2-bm1024-from512+slots-k4t8-bm256", slot_kernel<4, 8, 8, 8>(), 512, tall_kernel<8, 2, 16, 16>()},
-        {"tall-k8t2-bm1024-from512+slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 512, tall_kernel<8, 2, 16, 16>()},
+        {"tall-k8t4-bm512", tall_kernel<8, 4, 8, 16>(), 0, none},
+        {"tall-k8t4-bm512-from256+slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 256, tall_kernel<8, 4, 8, 16>()},
+        {"tall-k8t4-bm512-from384+slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 384, tall_kernel<8, 4, 8, 16>()},
+        {"tall-k8t4-bm512-from512+slots-k4t8-bm128", slot_kernel<4, 8, 4, 8>(), 512, tall_kernel<8, 4, 8, 16>()},
+        {"tall-k8t4-bm512-from256+slots-k4t8-bm256", slot_kernel<4, 8, 8, 8>(), 256, tall_kernel<8, 4, 8, 16>()},
     };
     return v;
 }

@@ -555,6 +555,177 @@ static MmaResult var_rate(int sms, bool check)
     return res;
 }
 
+// CTA-pair MMA (cta_group::2, M = 256 over a 2-CTA cluster, N = NN), one
+// stream issued by the first CTA: each CTA holds its 128 rows of A and its
+// NN / 2 rows of B in shared memory (the same offsets in both), the commit
+// arrives on the barrier at that offset in both CTAs.  KIND 0: kind::mxf4
+// (UE8M0 scale factors 1.0), 1: kind::f8f6f4.
+__device__ __forceinline__ uint32_t cl_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int KIND, int NN>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
+mma_pair(const uint8_t *Aimg, const uint8_t *Bimg, float *D, unsigned *status, int reps)
+{
+    constexpr int TBH = NN / 2 * 128;        // this CTA's half of the B image
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const uint32_t raw = smem_u32(sm);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *sb = sm + (base - raw);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sb + TA + TBH);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bar + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cl_rank();
+    const uint4 *ga = reinterpret_cast<const uint4 *>(Aimg + rank * TA);
+    const uint4 *gb = reinterpret_cast<const uint4 *>(Bimg + rank * TBH);
+    for (int i = threadIdx.x; i < (TA + TBH) / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(sb)[i] = i < TA / 16 ? ga[i] : gb[i - TA / 16];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tb = *slot;
+    if (KIND == 0) {
+        const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+        tmem_st32(tb + lanes + SFA_COL, 0x7F7F7F7Fu);
+        tmem_st32(tb + lanes + SFB_COL, 0x7F7F7F7Fu);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cl_sync();                               // both CTAs set up before the first MMA
+    tc_fence_after();
+    if (rank == 0 && threadIdx.x == 0) {
+        const uint32_t a0 = base, b0 = base + TA;
+        const uint32_t id = KIND == 0 ? idesc_mxf4(256, NN) : idesc_f8(256, NN);
+        for (int r = 0; r < reps; ++r) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t acc = (r > 0 || kk > 0) ? 1u : 0u;
+                const uint64_t ad = sdesc(a0 + kk * 32), bd = sdesc(b0 + kk * 32);
+                if (KIND == 0)
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
+                        "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
+                        ::"r"(tb), "l"(ad), "l"(bd), "r"(id), "r"(tb + SFA_COL), "r"(tb + SFB_COL), "r"(acc)
+                        : "memory");
+                else
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+                        ::"r"(tb), "l"(ad), "l"(bd), "r"(id), "r"(acc)
+                        : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+                     ::"r"(smem_u32(bar)), "h"((unsigned short)3) : "memory");
+    }
+    if (threadIdx.x == 0 && !mbar_wait_bounded(smem_u32(bar), 0, 4000000000ull)) atomicExch(status, 4u);
+    __syncthreads();
+    tc_fence_after();
+    if (D && blockIdx.x < 2) {
+        const uint32_t taddr = tb + ((uint32_t)(warp * 32) << 16);
+        for (int g = 0; g < NN / 32; ++g) {
+            uint32_t r[32];
+            tmem_ld32(taddr + 32 * g, r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int j = 0; j < 32; ++j)
+                D[(size_t)(rank * 128 + warp * 32 + lane) * 256 + 32 * g + j] = __uint_as_float(r[j]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cl_sync();                               // the peer's MMAs and reads are done
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tb), "r"(512) : "memory");
+}
+
+template <int KIND, int NN>
+static MmaResult pair_rate(int sms)
+{
+    MmaResult res;
+    const int K = KIND == 0 ? 256 : 128;
+    std::vector<uint8_t> abit(256 * K), bbit(256 * K);
+    uint64_t s = 4242 + KIND * 10 + NN;
+    for (auto &v : abit) v = sm64(s) & 1;
+    for (auto &v : bbit) v = (sm64(s) % 10) < 7;
+    std::vector<uint8_t> arow((size_t)256 * 128, 0), brow((size_t)256 * 128, 0);
+    auto put = [&](std::vector<uint8_t> &rows, int r, int k) {
+        if (KIND == 1) rows[(size_t)r * 128 + k] = 0x38;
+        else rows[(size_t)r * 128 + k / 2] |= (uint8_t)(0x2u << (4 * (k & 1)));
+    };
+    for (int r = 0; r < 256; ++r)
+        for (int k = 0; k < K; ++k) {
+            if (abit[(size_t)r * K + k]) put(arow, r, k);
+            if (bbit[(size_t)r * K + k]) put(brow, r, k);
+        }
+    std::vector<uint8_t> aimg, bimg;
+    swizzle_rows(arow, 256, aimg);
+    swizzle_rows(brow, 256, bimg);
+    uint8_t *dA, *dB;
+    float *dD;
+    unsigned *dst;
+    CK(cudaMalloc(&dA, 256 * 128)); CK(cudaMalloc(&dB, 256 * 128));
+    CK(cudaMalloc(&dD, 256 * 256 * 4)); CK(cudaMalloc(&dst, 4));
+    CK(cudaMemcpy(dA, aimg.data(), 256 * 128, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dB, bimg.data(), 256 * 128, cudaMemcpyHostToDevice));
+    CK(cudaMemset(dst, 0, 4));
+    CK(cudaMemset(dD, 0xFF, 256 * 256 * 4));
+    const int smem = 120 * 1024;
+    CK(cudaFuncSetAttribute(mma_pair<KIND, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    mma_pair<KIND, NN><<<2, 128, smem>>>(dA, dB, dD, dst, 1);
+    CK(cudaGetLastError());
+    CK(cudaDeviceSynchronize());
+    std::vector<float> Dh(256 * 256);
+    CK(cudaMemcpy(Dh.data(), dD, Dh.size() * 4, cudaMemcpyDeviceToHost));
+    res.wrong = 0;
+    for (int i = 0; i < 256; ++i)
+        for (int j = 0; j < NN; ++j) {
+            int e = 0;
+            for (int k = 0; k < K; ++k) e += abit[(size_t)i * K + k] & bbit[(size_t)j * K + k];
+            if (Dh[(size_t)i * 256 + j] != (float)e) ++res.wrong;
+        }
+    CK(cudaMemcpy(&res.status, dst, 4, cudaMemcpyDeviceToHost));
+    if (!res.wrong && !res.status) {
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        const int reps = 20000, grid = sms / 2 * 2;
+        for (int pass = 0; pass < 2; ++pass) {
+            CK(cudaEventRecord(e0));
+            mma_pair<KIND, NN><<<grid, 128, smem>>>(dA, dB, nullptr, dst, reps);
+            CK(cudaEventRecord(e1));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaGetLastError());
+            res.ms = run_ms(e0, e1);
+            res.tflops = 2.0 * 256 * NN * K * (double)reps * (grid / 2) / res.ms / 1e9;
+        }
+        CK(cudaMemcpy(&res.status, dst, 4, cudaMemcpyDeviceToHost));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    cudaFree(dA); cudaFree(dB); cudaFree(dD); cudaFree(dst);
+    return res;
+}
+
 static void print_mma(const char *name, const MmaResult &r, bool last)
 {
     printf("\"%s\": {\"wrong\": %ld, \"status\": %u, \"ms\": %.3f, \"tflops\": %.1f}%s", name, r.wrong, r.status,
@@ -650,6 +821,12 @@ int main()
     const MmaResult v1 = var_rate<2, 128>(sms, true);
     const MmaResult v2 = var_rate<1, 256>(sms, true);
     const MmaResult v3 = var_rate<3, 256>(sms, false);
+    const MmaResult p4_256 = pair_rate<0, 256>(sms);
+    const MmaResult p4_224 = pair_rate<0, 224>(sms);
+    const MmaResult p4_192 = pair_rate<0, 192>(sms);
+    const MmaResult p4_128 = pair_rate<0, 128>(sms);
+    const MmaResult p8_256 = pair_rate<1, 256>(sms);
+    const MmaResult p8_128 = pair_rate<1, 128>(sms);
     printf("{\"sms\": %d, \"max_sm_mhz\": %d, "
            "\"smem_lookup_tbs\": %.2f, \"smem_lookup_bytes_per_clk_per_sm\": %.1f, "
            "\"l2_ldg_tbs\": [%.2f, %.2f, %.2f], \"l2_ldg_ctas\": [%d, %d, %d], "
@@ -663,9 +840,18 @@ int main()
     print_mma("tcgen05_mxf4_m128n128", v0, false);
     print_mma("tcgen05_f8f6f4_m128n128", v1, false);
     print_mma("tcgen05_mxf4nvf4_4x_m128n256", v2, false);
-    print_mma("tcgen05_mxf4_a_in_tmem_m128n256", v3, true);
+    print_mma("tcgen05_mxf4_a_in_tmem_m128n256", v3, false);
+    print_mma("tcgen05_pair_mxf4_m256n256", p4_256, false);
+    print_mma("tcgen05_pair_mxf4_m256n224", p4_224, false);
+    print_mma("tcgen05_pair_mxf4_m256n192", p4_192, false);
+    print_mma("tcgen05_pair_mxf4_m256n128", p4_128, false);
+    print_mma("tcgen05_pair_f8f6f4_m256n256", p8_256, false);
+    print_mma("tcgen05_pair_f8f6f4_m256n128", p8_128, true);
     printf("}\n");
     const bool bad = f8.wrong || f4.wrong || v0.wrong || v1.wrong || v2.wrong || f8.status || f4.status ||
                      v0.status || v1.status || v2.status || v3.status || tma_status;
-    return bad ? 1 : 0;
+    const MmaResult *pairs[] = {&p4_256, &p4_224, &p4_192, &p4_128, &p8_256, &p8_128};
+    bool pair_bad = false;
+    for (const MmaResult *p : pairs) pair_bad = pair_bad || p->wrong || p->status;
+    return (bad || pair_bad) ? 1 : 0;
 }

@@ -142,11 +142,11 @@ def test_batched_table_bytes_follow_each_row_block_k():
     dims = [(1100, 64, 128), (1300, 64, 128), (200, 64, 128)]
     b, _ = bench.batched_table_bytes("slots-k4t8-bm256", dims)
     assert b == pytest.approx(sum(m * l * n for m, l, n in dims) / 32.0)
-    b, _ = bench.batched_table_bytes("tall-k8t2-bm1024-from256+slots-k4t8-bm128", dims)
+    b, _ = bench.batched_table_bytes("tall-k8t4-bm512-from256+slots-k4t8-bm128", dims)
     # 1100: 1024 tall + 76 rest; 1300: all tall (276 >= 256); 200: all rest
     want = (1024 * 64 * 128 / 64 + 76 * 64 * 128 / 32 + 1300 * 64 * 128 / 64 + 200 * 64 * 128 / 32)
     assert b == pytest.approx(want)
-    b, _ = bench.batched_table_bytes("tall-k8t2-bm1024-from512+slots-k4t8-bm256", dims)
+    b, _ = bench.batched_table_bytes("tall-k8t4-bm512-from512+slots-k4t8-bm256", dims)
     want = (1024 * 64 * 128 / 64 + 76 * 64 * 128 / 32 + 1024 * 64 * 128 / 64 + 276 * 64 * 128 / 32
             + 200 * 64 * 128 / 32)
     assert b == pytest.approx(want)

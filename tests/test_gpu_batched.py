@@ -47,11 +47,11 @@ def make_batch(dims, seed0):
     return dict(hostA=hostA, hostB=hostB, dA=dA, dB=dB, dC=dC, arrs=g.MatArrays(MC, MA, MB))
 
 
-# includes row counts past one 1024-row tall block with remainders below,
-# between and above the split thresholds (76, 276, 600 rows)
+# includes row counts past whole 512-row tall blocks with remainders below,
+# between and above the split thresholds (76, 276, 88, 406, 383 rows)
 RAGGED = [(1, 1, 1), (64, 64, 64), (65, 63, 129), (300, 700, 100), (1000, 90, 1030),
           (17, 2048, 5), (513, 257, 511), (2048, 300, 2048), (129, 1, 300), (7, 4000, 260),
-          (1100, 200, 300), (1300, 65, 700), (1624, 33, 130)]
+          (1100, 200, 300), (1300, 65, 700), (1624, 33, 130), (1430, 97, 260), (895, 50, 70)]
 
 
 NVARIANTS = 16   # 8 one-product-per-tile, 3 slot-packed, 1 tall slot-packed, 4 split variants
