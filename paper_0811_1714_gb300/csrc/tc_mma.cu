@@ -116,8 +116,8 @@ template <> struct Fmt<KIND_F4> {
     // with the scale factors beside them, 256-column tiles have room for one
     // accumulator, 224- and 128-column tiles for two
     static constexpr int nacc(int TN) { return TN == 256 ? 1 : 2; }
-    // one accumulator: every chunk boundary idles the tensor core while the
-    // epilogue reads it out, so the chunks are twice as long (sums <= 2^13)
+    // chunks of 8192 entries (sums <= 2^13, exact with 13 significant bits):
+    // one accumulator hand-off per tile of a depth-2 leaf of n = 32768
     static constexpr int KCHUNK = 8192;
     // block-scaled descriptor: scale-factor ids 0 (bits 4-5, 29-30), A = B =
     // E2M1 (code 1 at bits 7-9 and 10-12), both K-major, N >> 3 at bits
@@ -169,7 +169,7 @@ struct Tile {
 // and B^T rows 0-127 from its shared memory, rows 128-255 from its peer's,
 // each CTA's accumulator rows in its own tensor memory).
 template <int KIND, int PAIR, int TN>
-__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t ad, uint64_t bd, uint32_t tmem_base, uint32_t acc)
+__device__ __forceinline__ void mma_issue(uint32_t d, uint64_t ad, uint64_t bd, uint32_t sfa, uint32_t sfb, uint32_t acc)
 {
     constexpr uint32_t ID = Fmt<KIND>::idesc(PAIR ? 2 * BM : BM, TN);
     if (KIND == KIND_F8) {
@@ -185,14 +185,12 @@ __device__ __forceinline__ void mma_issue(uint32_t d, uint64_t ad, uint64_t bd, 
         if (PAIR)
             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
                          "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
-                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + Cols<TN>::SFA),
-                           "r"(tmem_base + Cols<TN>::SFB), "r"(acc)
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(sfa), "r"(sfb), "r"(acc)
                          : "memory");
         else
             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %6, 0;\n\t"
                          "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n\t}"
-                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(tmem_base + Cols<TN>::SFA),
-                           "r"(tmem_base + Cols<TN>::SFB), "r"(acc)
+                         ::"r"(d), "l"(ad), "l"(bd), "r"(ID), "r"(sfa), "r"(sfb), "r"(acc)
                          : "memory");
     }
 }
@@ -248,13 +246,34 @@ __device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap
         : "memory");
 }
 
+// Tile t of a uniform batch: leaf b, then bands of GM tile rows, each band
+// walked column by column (GM tiles of one column, then the next), so that
+// the tiles the CTAs run at one time share a few row blocks of A and column
+// blocks of B^T in L2 (a band of 8 x ~10 tiles for 76 pairs) instead of
+// streaming all of B^T once per row block when a leaf exceeds the L2.
+constexpr int GM = 8;
+
 __device__ __forceinline__ void tile_coords(const Params &P, int64_t t, int &b, int &tm, int &tn)
 {
     const int64_t per = (int64_t)P.tiles_m * P.tiles_n;
-    b = (int)(t / per);
-    const int64_t r = t - (int64_t)b * per;
-    tm = (int)(r / P.tiles_n);
-    tn = (int)(r - (int64_t)tm * P.tiles_n);
+    int64_t r;
+    if (per * P.batch <= 0x7FFFFFFF) {
+        // 32-bit divisions (the 64-bit ones are long subroutines)
+        const uint32_t tt = (uint32_t)t, pp = (uint32_t)per;
+        b = (int)(tt / pp);
+        r = (int64_t)(tt - (uint32_t)b * pp);
+    } else {
+        b = (int)(t / per);
+        r = t - (int64_t)b * per;
+    }
+    const uint32_t band_tiles = (uint32_t)GM * (uint32_t)P.tiles_n;
+    const uint32_t band = (uint32_t)r / band_tiles;
+    const uint32_t in = (uint32_t)r - band * band_tiles;
+    const uint32_t left = (uint32_t)P.tiles_m - band * GM;
+    const uint32_t rows = left < (uint32_t)GM ? left : (uint32_t)GM;      // tile rows of this band
+    const uint32_t col = in / rows;
+    tm = (int)(band * GM + (in - col * rows));
+    tn = (int)col;
 }
 
 __device__ __forceinline__ Tile get_tile(const Params &P, const CUtensorMap *ma, const CUtensorMap *mb, int64_t t)
@@ -448,8 +467,11 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     } else if (warp == MMA_WARP) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0 && rank == 0) {
-            uint32_t it = 0, u = 0;                      // stages, accumulator uses
+            uint32_t u = 0;                              // accumulator uses
+            int s = 0;                                   // ring stage and its phase bit
+            uint32_t ph = 0;
             bool ok = true;
+            const uint32_t sfa = tmem_base + Cols<TN>::SFA, sfb = tmem_base + Cols<TN>::SFB;
             for (int64_t t = t0; t < tiles && ok; t += tstep) {
                 const Tile T = get_tile(P, &mapA, &mapB, t);
                 const int64_t nst = (T.nkb + KBS - 1) / KBS;
@@ -464,22 +486,29 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     const uint32_t dt = tmem_base + (uint32_t)ab * Cols<TN>::ACC;
                     const int64_t ks0 = (int64_t)c * SPC;
                     const int64_t ks1 = std::min<int64_t>(nst, ks0 + SPC);
-                    for (int64_t ks = ks0; ks < ks1; ++ks, ++it) {
-                        const int s = (int)(it % STAGES);
-                        if (!mbar_wait(full_bar(s), (it / STAGES) & 1u, P.status, abort_flag)) {
+                    for (int64_t ks = ks0; ks < ks1; ++ks) {
+                        if (!mbar_wait(full_bar(s), ph, P.status, abort_flag)) {
                             ok = false;
                             break;
                         }
                         fence_after();
-                        const uint32_t sa = base + s * STAGE_BYTES, sb = sa + KBS * R::A_SUB;
+                        // descriptors of the stage's first K block; the others are
+                        // constant offsets (start address >> 4 in the low bits)
+                        const uint64_t da = smem_desc_sw128(base + s * STAGE_BYTES);
+                        const uint64_t db = da + (uint64_t)((KBS * R::A_SUB) >> 4);
+                        const uint32_t acc0 = ks > ks0 ? 1u : 0u;
 #pragma unroll
                         for (int j = 0; j < KBS; ++j)
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per instruction
-                                mma_issue<KIND, PAIR, TN>(dt, smem_desc_sw128(sa + j * R::A_SUB + kk * 32),
-                                                      smem_desc_sw128(sb + j * R::B_SUB + kk * 32), tmem_base,
-                                                      (ks > ks0 || j > 0 || kk > 0) ? 1u : 0u);
+                                mma_issue<KIND, PAIR, TN>(dt, da + (uint64_t)((j * R::A_SUB + kk * 32) >> 4),
+                                                          db + (uint64_t)((j * R::B_SUB + kk * 32) >> 4), sfa, sfb,
+                                                          (j > 0 || kk > 0) ? 1u : acc0);
                         commit<PAIR>(empty_bar(s), 3);     // stage free (in both CTAs) once these MMAs read it
+                        if (++s == STAGES) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
                     }
                     if (!ok) break;
                     commit<PAIR>(tfull_bar(ab), 3);        // accumulator ready for the epilogue(s)
