@@ -472,6 +472,8 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             uint32_t ph = 0;
             bool ok = true;
             const uint32_t sfa = tmem_base + Cols<TN>::SFA, sfb = tmem_base + Cols<TN>::SFB;
+            const uint64_t da_first = smem_desc_sw128(base);
+            uint64_t da = da_first, db = da_first + (uint64_t)((KBS * R::A_SUB) >> 4);
             for (int64_t t = t0; t < tiles && ok; t += tstep) {
                 const Tile T = get_tile(P, &mapA, &mapB, t);
                 const int64_t nst = (T.nkb + KBS - 1) / KBS;
@@ -487,15 +489,13 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                     const int64_t ks0 = (int64_t)c * SPC;
                     const int64_t ks1 = std::min<int64_t>(nst, ks0 + SPC);
                     for (int64_t ks = ks0; ks < ks1; ++ks) {
-                        if (!mbar_wait(full_bar(s), ph, P.status, abort_flag)) {
+                        // the MMA pipe idles while this thread does anything but
+                        // issue MMAs: between stages, a non-blocking test first
+                        if (!mbar_test_wait(full_bar(s), ph) && !mbar_wait(full_bar(s), ph, P.status, abort_flag)) {
                             ok = false;
                             break;
                         }
                         fence_after();
-                        // descriptors of the stage's first K block; the others are
-                        // constant offsets (start address >> 4 in the low bits)
-                        const uint64_t da = smem_desc_sw128(base + s * STAGE_BYTES);
-                        const uint64_t db = da + (uint64_t)((KBS * R::A_SUB) >> 4);
                         const uint32_t acc0 = ks > ks0 ? 1u : 0u;
 #pragma unroll
                         for (int j = 0; j < KBS; ++j)
@@ -505,10 +505,16 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                                                           db + (uint64_t)((j * R::B_SUB + kk * 32) >> 4), sfa, sfb,
                                                           (j > 0 || kk > 0) ? 1u : acc0);
                         commit<PAIR>(empty_bar(s), 3);     // stage free (in both CTAs) once these MMAs read it
+                        // descriptors of the next stage's first K block (the others are
+                        // constant offsets: start address >> 4 in the low bits)
                         if (++s == STAGES) {
                             s = 0;
                             ph ^= 1u;
+                            da = da_first;
+                        } else {
+                            da += (uint64_t)(STAGE_BYTES >> 4);
                         }
+                        db = da + (uint64_t)((KBS * R::A_SUB) >> 4);
                     }
                     if (!ok) break;
                     commit<PAIR>(tfull_bar(ab), 3);        // accumulator ready for the epilogue(s)
