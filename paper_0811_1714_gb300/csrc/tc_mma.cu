@@ -639,44 +639,70 @@ __device__ __forceinline__ uint32_t f4_of_byte(uint32_t v)
 
 // Rows of a batch of packed matrices (rows x cols, stride ld, batch stride
 // bs words) -> rows of `rowbytes` expanded bytes (entries beyond cols 0),
-// row f = b * rows + r at Y + f * rowbytes.  A warp takes 32 consecutive
-// words of a row (one coalesced 256-byte load) and writes their expansion as
-// 16-byte chunks, chunk c of the group by lane c mod 32 (each store
-// instruction writes 512 contiguous bytes); the word a chunk comes from is
-// fetched from its lane by a shuffle.
+// row f = b * rows + r at Y + f * rowbytes.  A warp takes whole rows; per
+// group of 32 consecutive words of the row (one coalesced 256-byte load,
+// the loads of up to four groups issued before any store) it writes their
+// expansion as 16-byte chunks, chunk c of the group by lane c mod 32 (each
+// store instruction writes 512 contiguous bytes); the word a chunk comes
+// from is fetched from its lane by a shuffle.
+template <int KIND>
+__device__ __forceinline__ uint4 expand_chunk(uint64_t xs, int c)
+{
+    if (KIND == KIND_F8) {
+        const uint32_t h = (uint32_t)(xs >> (16 * (c & 3)));
+        return make_uint4(f8_of_nibble(h & 15u), f8_of_nibble((h >> 4) & 15u), f8_of_nibble((h >> 8) & 15u),
+                          f8_of_nibble((h >> 12) & 15u));
+    }
+    const uint32_t h = (uint32_t)(xs >> (32 * (c & 1)));
+    return make_uint4(f4_of_byte(h), f4_of_byte(h >> 8), f4_of_byte(h >> 16), f4_of_byte(h >> 24));
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256)
 expand_kernel(const uint64_t *__restrict__ X, int64_t ld, int64_t bs, int64_t rows, int64_t cols, int64_t nrows,
               uint8_t *__restrict__ Y, int64_t rowbytes)
 {
     constexpr int CPW = KIND == KIND_F8 ? 4 : 2;                     // 16-byte chunks per packed word
+    constexpr int U = 4;                                             // groups whose loads are in flight
     const int lane = threadIdx.x & 31;
     const int64_t W = words_of(cols);
     const int64_t kpw = rowbytes / (16 * CPW);                       // packed words per expanded row
-    const int64_t ngroups = (kpw + 31) / 32;
-    const int64_t items = nrows * ngroups;
+    const int ngroups = (int)((kpw + 31) / 32);
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < items; it += nwarps) {
-        const int64_t f = it / ngroups, wg = it - f * ngroups;
-        const int64_t b = f / rows, r = f - b * rows;
-        const int64_t w = wg * 32 + lane;
-        const uint64_t x = (w < W) ? (X[b * bs + r * ld + w] & word_mask(w, cols)) : 0ull;
-        uint4 *o = reinterpret_cast<uint4 *>(Y + f * rowbytes) + wg * 32 * CPW;
-        const int64_t left = (kpw - wg * 32) * CPW;                   // chunks of this row from here on
+    const bool small = nrows <= 0x7FFFFFFF && rows <= 0x7FFFFFFF;
+    for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < nrows; f += nwarps) {
+        int64_t b, r;
+        if (small) {
+            // 32-bit division (the 64-bit one is a long subroutine)
+            const uint32_t bb = (uint32_t)f / (uint32_t)rows;
+            b = bb;
+            r = (int64_t)((uint32_t)f - bb * (uint32_t)rows);
+        } else {
+            b = f / rows;
+            r = f - b * rows;
+        }
+        const uint64_t *xr = X + b * bs + r * ld;
+        uint4 *orow = reinterpret_cast<uint4 *>(Y + f * rowbytes);
+        for (int g0 = 0; g0 < ngroups; g0 += U) {
+            uint64_t x[U];
 #pragma unroll
-        for (int q = 0; q < CPW; ++q) {
-            const int c = 32 * q + lane;                              // chunk of the group
-            const uint64_t xs = __shfl_sync(0xffffffffu, x, c / CPW);
-            uint4 v;
-            if (KIND == KIND_F8) {
-                const uint32_t h = (uint32_t)(xs >> (16 * (c & 3)));
-                v = make_uint4(f8_of_nibble(h & 15u), f8_of_nibble((h >> 4) & 15u), f8_of_nibble((h >> 8) & 15u),
-                               f8_of_nibble((h >> 12) & 15u));
-            } else {
-                const uint32_t h = (uint32_t)(xs >> (32 * (c & 1)));
-                v = make_uint4(f4_of_byte(h), f4_of_byte(h >> 8), f4_of_byte(h >> 16), f4_of_byte(h >> 24));
+            for (int u = 0; u < U; ++u) {
+                const int64_t w = (int64_t)(g0 + u) * 32 + lane;
+                x[u] = (g0 + u < ngroups && w < W) ? (xr[w] & word_mask(w, cols)) : 0ull;
             }
-            if (c < left) o[c] = v;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int wg = g0 + u;
+                if (wg >= ngroups) break;
+                uint4 *o = orow + (int64_t)wg * 32 * CPW;
+                const int64_t left = (kpw - (int64_t)wg * 32) * CPW;   // chunks of this row from here on
+#pragma unroll
+                for (int q = 0; q < CPW; ++q) {
+                    const int c = 32 * q + lane;                      // chunk of the group
+                    const uint64_t xs = __shfl_sync(0xffffffffu, x[u], c / CPW);
+                    if (c < left) o[c] = expand_chunk<KIND>(xs, c);
+                }
+            }
         }
     }
 }
@@ -1190,9 +1216,7 @@ int tc_expand_launch(int kind, const uint64_t *X, int64_t ld, int64_t bs, int64_
     int dev = 0, sms = 0;
     GF2_CUDA_TRY(cudaGetDevice(&dev));
     GF2_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t epr = kind == KIND_F8 ? 128 : 256;
-    const int64_t groups = nrows * ((rowbytes / ROWB * epr / 64 + 31) / 32);   // 32-word groups
-    const int64_t want = (groups + 7) / 8;                 // 8 warps per block, one group each
+    const int64_t want = (nrows + 7) / 8;                  // 8 warps per block, one row each
     const int64_t grid = std::min<int64_t>(want, (int64_t)sms * 16);
     ProfScope ps(PF_EXPAND, s);
     if (kind == KIND_F8)

@@ -140,41 +140,75 @@ __global__ void seeded_words_kernel(uint64_t *X, int64_t n, uint64_t seed)
         X[i] = sm64(seed, (uint64_t)i + 1);
 }
 
-// T = X^T, one warp per 64 x 64 block: lane i holds rows i and i+32 of the
-// block; a ballot over the lanes of bit j gathers column j.
-__global__ void transpose_kernel(DMat T, DMat X)
+// Transpose of a 32 x 32 bit block held by a warp, lane = row, bit j of the
+// lane's word = column j: five exchange steps of the standard recursive
+// block swap (blocks of 16, 8, 4, 2, 1), partner lane ^ w by a shuffle.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
+{
+    const uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        const int w = 16 >> st;
+        const uint32_t m = M[st];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, w);
+        x = (lane & w) ? ((x & ~m) | ((y >> w) & m)) : ((x & m) | ((y & m) << w));
+    }
+    return x;
+}
+
+// T = X^T, one warp per 256 x 256 block (256 rows x 4 words of X): lane i
+// holds rows i + 32 k (k < 8) of the block, 4 words each, so every row's 32
+// bytes are read by one lane (whole sectors); each 64 x 64 sub-block is four
+// 32 x 32 shuffle transposes with its off-diagonal quarters swapped, and
+// lane i ends with 4 consecutive words of 8 rows of T, written whole.
+__global__ void __launch_bounds__(256) transpose_kernel(DMat T, DMat X)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t RB = (X.rows + 63) / 64;          // row blocks of X
-    const int64_t CB = words_of(X.cols);            // column blocks (words) of X
+    const int64_t RB = (X.rows + 255) / 256;         // 256-row blocks of X
+    const int64_t XW = words_of(X.cols);
+    const int64_t CB = (XW + 3) / 4;                 // 4-word column blocks of X
+    const int64_t TW = words_of(T.cols);
     const int64_t nblk = RB * CB;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = warp_global; b < nblk; b += nwarps) {
-        const int64_t rb = b / CB, cb = b - rb * CB;
-        const int64_t r0 = rb * 64 + lane, r1 = r0 + 32;
-        const uint64_t cm = word_mask(cb, X.cols);
-        const uint64_t x0 = (r0 < X.rows) ? (X.p[r0 * X.ld + cb] & cm) : 0ull;
-        const uint64_t x1 = (r1 < X.rows) ? (X.p[r1 * X.ld + cb] & cm) : 0ull;
-        uint64_t out0 = 0, out1 = 0;
-#pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-            const uint32_t a = __ballot_sync(0xffffffffu, (x0 >> j) & 1);
-            const uint32_t c = __ballot_sync(0xffffffffu, (x1 >> j) & 1);
-            const uint32_t d = __ballot_sync(0xffffffffu, (x0 >> (j + 32)) & 1);
-            const uint32_t e = __ballot_sync(0xffffffffu, (x1 >> (j + 32)) & 1);
-            if (lane == j) {
-                out0 = (uint64_t)a | ((uint64_t)c << 32);
-                out1 = (uint64_t)d | ((uint64_t)e << 32);
+    for (int64_t blk = warp_global; blk < nblk; blk += nwarps) {
+        const int64_t rb = blk / CB, cb = blk - rb * CB;
+        uint64_t x[8][4];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t r = rb * 256 + 32 * k + lane;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t w = cb * 4 + c;
+                x[k][c] = (r < X.rows && w < XW) ? (X.p[r * X.ld + w] & word_mask(w, X.cols)) : 0ull;
             }
         }
-        // out0: row cb*64+lane of T, word rb; out1: row cb*64+32+lane
-        const uint64_t tm = word_mask(rb, T.cols);
-        out0 &= tm;
-        out1 &= tm;
-        const int64_t t0 = cb * 64 + lane, t1 = t0 + 32;
-        if (t0 < T.rows) T.p[t0 * T.ld + rb] = out0;
-        if (t1 < T.rows) T.p[t1 * T.ld + rb] = out1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            // rows (cb * 4 + c) * 64 + lane (h = 0) and + 32 (h = 1) of T, words rb * 4 + q
+            uint64_t o[2][4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                // sub-block: rows 64 q + lane (x0) and 64 q + 32 + lane (x1) of the block, word c
+                const uint64_t x0 = x[2 * q][c], x1 = x[2 * q + 1][c];
+                const uint32_t a = transpose32((uint32_t)x0, lane);           // rows 0-31, cols 0-31
+                const uint32_t b = transpose32((uint32_t)x1, lane);           // rows 32-63, cols 0-31
+                const uint32_t d = transpose32((uint32_t)(x0 >> 32), lane);   // rows 0-31, cols 32-63
+                const uint32_t e = transpose32((uint32_t)(x1 >> 32), lane);   // rows 32-63, cols 32-63
+                o[0][q] = (uint64_t)a | ((uint64_t)b << 32);
+                o[1][q] = (uint64_t)d | ((uint64_t)e << 32);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t t = (cb * 4 + c) * 64 + 32 * h + lane;
+                if (t >= T.rows) continue;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t w = rb * 4 + q;
+                    if (w < TW) T.p[t * T.ld + w] = o[h][q] & word_mask(w, T.cols);
+                }
+            }
+        }
     }
 }
 
@@ -291,10 +325,10 @@ int seeded_words_launch(uint64_t *X, int64_t n, uint64_t seed, cudaStream_t s)
 
 int transpose_launch(DMat T, DMat X, cudaStream_t s)
 {
-    const int64_t nblk = ((X.rows + 63) / 64) * words_of(X.cols);
+    const int64_t nblk = ((X.rows + 255) / 256) * ((words_of(X.cols) + 3) / 4);
     if (nblk <= 0) return GF2_OK;
     int64_t blocks = (nblk * 32 + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > 152 * 16) blocks = 152 * 16;
     ProfScope ps(PF_TRANSPOSE, s);
     transpose_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, X);
     note_launch();

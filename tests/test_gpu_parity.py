@@ -256,13 +256,22 @@ def test_make_table_matches_gray_code_table(k):
 
 # ---------------------------------------------------------------- helpers of the path
 
-def test_transpose():
-    X = synth.random_packed(300, 700, 4)
-    T = g.empty(700, 300)
+@pytest.mark.parametrize("r,c", [(300, 700), (1, 1), (64, 64), (256, 256), (257, 1025), (1000, 64),
+                                 (64, 3000), (511, 513), (2048, 300)])
+def test_transpose(r, c):
+    """The packed transpose (256 x 256-entry warp tiles): every entry, ragged
+    tiles on both sides, and the bits past T's last column written as zero."""
+    X = synth.random_packed(r, c, 4)
+    T = g.empty(c, r)
+    T.fill_(-1)
     Xd = to_dev(X)
-    g.gf2_transpose(g.mat(T, 300), g.mat(Xd, 700))
+    g.gf2_transpose(g.mat(T, r), g.mat(Xd, c))
     torch.cuda.synchronize()
-    assert np.array_equal(synth.unpack_bits(to_host(T), 300), synth.unpack_bits(X, 700).T)
+    got = to_host(T)
+    assert np.array_equal(synth.unpack_bits(got, r), synth.unpack_bits(X, c).T)
+    W = synth.words_for(r)
+    if r % 64:
+        assert np.all((got[:, W - 1] & ~synth.tail_mask(r)) == 0)
 
 
 def test_freivalds_accepts_and_rejects():
