@@ -11,14 +11,17 @@
 //  * slot-packed: the 8 sixteen-byte lane chunks of a 1024-column tile are
 //    128-column slices of up to 8 different products, each lane working on
 //    its own slot's A rows, B rows, masks and C (m4rm_slots_kernel), so that
-//    narrow products do not leave most of a tile empty.
+//    narrow products do not leave most of a tile empty;
+//  * tall slot-packed: the same slots over 512 rows with k = 8 tables
+//    (m4rm_tall_slots_kernel), for the tall row blocks of a batch.
 // Tiles are ordered by decreasing K extent (longest first) so the queue
-// drains evenly.
+// drains evenly.  A split variant runs the tall row blocks on the tall
+// kernel and the rest on the slot kernel, two kernel nodes of one graph.
 //
 // Host side (gf2_mul_batched): the first call for a set of operands builds
 // the descriptor tables, lets the autotuner time every candidate variant on
 // that batch (candidates differ in k, t, tile rows BM and tile width), keeps
-// the fastest, and builds a CUDA graph {reset counter, persistent kernel}.
+// the fastest, and builds a CUDA graph {reset counters, persistent kernel(s)}.
 // Later calls with the same operands replay the graph.  The autotuner's
 // choices are cached per shape signature, and can be persisted to the JSON
 // file named by the GF2_TUNE_CACHE environment variable.
