@@ -294,14 +294,15 @@ std::string plan_text(const Plan &p)
 // Base case over `batch` products with dense or user layouts.
 int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const uint64_t *B,
              int64_t ldb, int64_t bsB, uint64_t *C, int64_t ldc, int64_t bsC, int64_t m, int64_t l,
-             int64_t n, int batch, int accumulate, char *scratch, cudaStream_t s)
+             int64_t n, int batch, int accumulate, char *scratch, cudaStream_t s, bool a_expanded = false)
 {
     if (is_expanded(p.base)) {
         // expand the packed leaves once (HBM-bound), then the MMA kernel
+        // (A's leaves already expanded when a_expanded)
         const int kind = kind_of(p.base);
         uint8_t *XA = reinterpret_cast<uint8_t *>(scratch + p.offXA);
         uint8_t *XB = reinterpret_cast<uint8_t *>(scratch + p.offXB);
-        int rc = tc_expand_launch(kind, A, lda, bsA, m, l, batch, XA, p.rowbytes, s);
+        int rc = a_expanded ? GF2_OK : tc_expand_launch(kind, A, lda, bsA, m, l, batch, XA, p.rowbytes, s);
         if (!rc) rc = tc_expand_launch(kind, B, ldb, bsB, n, l, batch, XB, p.rowbytes, s);
         if (rc) return rc;
         TcxLaunch X;
@@ -374,6 +375,21 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
             j += step;
         }
     }
+    // the expanded tensor-core base cases: A's leaves are expanded before B
+    // is needed, so that this runs while B is still arriving
+    bool a_expanded = false;
+    if (is_expanded(p.base) && !(d == 0 && p.cubic)) {
+        int64_t cntA = 1;
+        for (int j = 0; j < d; ++j) cntA *= 7;
+        const uint64_t *XA = d == 0 ? A->data : reinterpret_cast<const uint64_t *>(scratch + p.offA[d]);
+        const int64_t ldXA = d == 0 ? A->stride_words : p.ldA[d];
+        const int64_t bsXA = d == 0 ? 0 : p.slabA[d];
+        const int64_t Md = d == 0 ? m : p.M >> d, Ld = d == 0 ? l : p.L >> d;
+        const int rc = tc_expand_launch(kind_of(p.base), XA, ldXA, bsXA, Md, Ld, (int)cntA,
+                                        reinterpret_cast<uint8_t *>(scratch + p.offXA), p.rowbytes, s);
+        if (rc) return rc;
+        a_expanded = true;
+    }
     if (b_ready) GF2_CUDA_TRY(cudaStreamWaitEvent(s, b_ready, 0));
     // the tensor-core base cases read B transposed
     if (tc) {
@@ -397,7 +413,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     }
     if (d == 0)
         return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
-                        m, l, n, 1, accumulate, scratch, s);
+                        m, l, n, 1, accumulate, scratch, s, a_expanded);
 
     // top-down: the additions of Algorithm 4 (the left factor's above, the
     // right factor's here) for every sub-problem of each level; two levels
@@ -443,7 +459,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         int rc = run_base(p, reinterpret_cast<const uint64_t *>(scratch + p.offA[d]), p.ldA[d], p.slabA[d],
                           reinterpret_cast<const uint64_t *>(scratch + p.offB[d]), p.ldB[d], p.slabB[d],
                           reinterpret_cast<uint64_t *>(scratch + p.offP[d]), p.ldP[d], p.slabP[d], Md, Ld,
-                          Nd, (int)cnt, 0, scratch, s);
+                          Nd, (int)cnt, 0, scratch, s, a_expanded);
         if (rc) return rc;
     }
     // bottom-up: the 7 final additions of Algorithm 4, Augment and Stack,

@@ -261,6 +261,26 @@ __global__ void __launch_bounds__(256) smem_lookup(int iters, uint4 *out)
 }
 
 // ---- mma.sync rates (register operands, 8 independent accumulators per warp)
+// ---- integer LOP3 rate (the XORs of the lookup-accumulate): 8 independent
+// 3-input XOR chains per thread, one lop3.b32 per step, full occupancy
+__global__ void __launch_bounds__(256) lop3_rate(int iters, uint32_t *out)
+{
+    const uint32_t b = threadIdx.x * 0x9E3779B9u + blockIdx.x, c = b ^ 0x7F4A7C15u;
+    uint32_t a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = b + (uint32_t)i * 0x01000193u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(a[i]) : "r"(b), "r"(c));
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x ^= a[i];
+    if (x == 0x2545F491u) out[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
 template <bool B1>
 __global__ void __launch_bounds__(256) mma_sync_rate(int iters, int *out)
 {
@@ -815,6 +835,20 @@ int main()
         }
         cudaFree(out);
     }
+    double lop3_per_s = 0;
+    {
+        uint32_t *out;
+        CK(cudaMalloc(&out, (size_t)sms * 8 * 256 * 4));
+        const int iters = 20000;
+        lop3_rate<<<sms * 8, 256>>>(10, out);
+        CK(cudaEventRecord(e0));
+        lop3_rate<<<sms * 8, 256>>>(iters, out);
+        CK(cudaEventRecord(e1));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaGetLastError());
+        lop3_per_s = (double)sms * 8 * 256 * iters * 32.0 / (run_ms(e0, e1) * 1e-3);
+        cudaFree(out);
+    }
     const MmaResult f8 = mma_rate<1>(sms);
     const MmaResult f4 = mma_rate<0>(sms);
     const MmaResult v0 = var_rate<0, 128>(sms, true);
@@ -831,10 +865,11 @@ int main()
            "\"smem_lookup_tbs\": %.2f, \"smem_lookup_bytes_per_clk_per_sm\": %.1f, "
            "\"l2_ldg_tbs\": [%.2f, %.2f, %.2f], \"l2_ldg_ctas\": [%d, %d, %d], "
            "\"l2_tma_bulk_tbs\": [%.2f, %.2f], \"l2_tma_ctas\": [%d, %d], \"l2_tma_status\": %u, "
-           "\"mma_sync_s8_tops\": %.1f, \"mma_sync_b1_tops\": %.1f, ",
+           "\"mma_sync_s8_tops\": %.1f, \"mma_sync_b1_tops\": %.1f, "
+           "\"lop3_per_s\": %.4g, \"lop3_per_clk_per_sm\": %.1f, ",
            sms, khz / 1000, smem_tbs, smem_tbs * 1e12 / sms / (khz * 1e3), l2_ldg_tbs[0], l2_ldg_tbs[1],
            l2_ldg_tbs[2], sms, 2 * sms, 4 * sms, l2_tma_tbs[0], l2_tma_tbs[1], sms, 2 * sms, tma_status,
-           sync_tops[0], sync_tops[1]);
+           sync_tops[0], sync_tops[1], lop3_per_s, lop3_per_s / sms / (khz * 1e3));
     print_mma("tcgen05_f8f6f4_m128n256", f8, false);
     print_mma("tcgen05_mxf4_m128n256", f4, false);
     print_mma("tcgen05_mxf4_m128n128", v0, false);
