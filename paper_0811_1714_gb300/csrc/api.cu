@@ -65,17 +65,18 @@ std::map<std::pair<int, uintptr_t>, std::shared_ptr<Arena>> g_arenas;
 
 // One non-blocking side stream per device (created on first use), for
 // copies that overlap work on the caller's stream; ordered by events.
-cudaStream_t side_stream(int dev)
+cudaStream_t side_stream(int dev, int which = 0)
 {
     static std::mutex mu;
-    static cudaStream_t st[64] = {};
-    if (dev < 0 || dev >= 64) return nullptr;
+    static cudaStream_t st[64][2] = {};
+    if (dev < 0 || dev >= 64 || which < 0 || which > 1) return nullptr;
     std::lock_guard<std::mutex> lk(mu);
-    if (!st[dev] && cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaStream_t &x = st[dev][which];
+    if (!x && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        st[dev] = nullptr;
+        x = nullptr;
     }
-    return st[dev];
+    return x;
 }
 
 struct ArenaHold {
@@ -333,7 +334,7 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
 
 // C = A B (or C ^= A B) for device matrices on the current device.
 int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan &p, int accumulate,
-               char *scratch, cudaStream_t s, cudaEvent_t b_ready = nullptr)
+               char *scratch, cudaStream_t s, cudaEvent_t b_ready = nullptr, bool bt_ready = false)
 {
     const int64_t m = p.m, l = p.l, n = p.n;
     if (m == 0 || n == 0) return GF2_OK;
@@ -394,10 +395,12 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     // the tensor-core base cases read B transposed
     if (tc) {
         uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
-        DMat T{Bt, n, l, p.ldBt};
-        DMat X{B->data, l, n, B->stride_words};
-        int rc = transpose_launch(T, X, s);
-        if (rc) return rc;
+        if (!bt_ready) {
+            DMat T{Bt, n, l, p.ldBt};
+            DMat X{B->data, l, n, B->stride_words};
+            int rc = transpose_launch(T, X, s);
+            if (rc) return rc;
+        }
         Bsrc = Bt;
         ldBsrc = p.ldBt;
     }
@@ -961,6 +964,7 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
     char *base = static_cast<char *>(scratch);
 
     gf2_mat dA = *A, dB = *B, dC = *C;
+    bool bt_ready = false;                   // B^T already in the plan's scratch
     // with both factors on the host, B is copied on a side stream while the
     // left factor's Strassen-Winograd additions run (they need only A)
     cudaEvent_t b_ready = nullptr, s_ready = nullptr;
@@ -997,9 +1001,39 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
         dB.data = reinterpret_cast<uint64_t *>(base + offB);
         dB.stride_words = even_up(words_of(n));
         dB.device = dev;
-        GF2_CUDA_TRY(cudaMemcpy2DAsync(dB.data, dB.stride_words * 8, B->data, B->stride_words * 8,
-                                       words_of(n) * 8, l, cudaMemcpyHostToDevice, sB));
-        if (b_ready) GF2_CUDA_TRY(cudaEventRecord(b_ready, sB));
+        cudaStream_t sT = (b_ready && !tuning && is_tc(plans[0].base) && !plans[0].cubic) ? side_stream(dev, 1)
+                                                                                           : nullptr;
+        if (sT) {
+            // the tensor-core base cases read B transposed: B is copied in row
+            // blocks on one side stream, and each block is transposed on a
+            // second one while the next crosses the link (row block [r0, r1)
+            // of B is columns [r0, r1) of B^T, words r0 / 64 onwards of its
+            // rows)
+            uint64_t *Bt = reinterpret_cast<uint64_t *>(base + plans[0].offBt);
+            const int64_t ch = std::max<int64_t>(256, (l / 8 + 255) / 256 * 256);
+            for (int64_t r0 = 0; r0 < l; r0 += ch) {
+                const int64_t r1 = std::min(l, r0 + ch);
+                uint64_t *dst = dB.data + r0 * dB.stride_words;
+                GF2_CUDA_TRY(cudaMemcpy2DAsync(dst, dB.stride_words * 8, B->data + r0 * B->stride_words,
+                                               B->stride_words * 8, words_of(n) * 8, r1 - r0,
+                                               cudaMemcpyHostToDevice, sB));
+                cudaEvent_t landed = nullptr;
+                GF2_CUDA_TRY(cudaEventCreateWithFlags(&landed, cudaEventDisableTiming));
+                const cudaError_t e1 = cudaEventRecord(landed, sB);
+                const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(sT, landed, 0) : e1;
+                cudaEventDestroy(landed);                 // released once the wait has passed
+                if (e2 != cudaSuccess) return GF2_ECUDA;
+                DMat T{Bt + r0 / 64, n, r1 - r0, plans[0].ldBt};
+                DMat X{dst, r1 - r0, n, dB.stride_words};
+                if ((rc = transpose_launch(T, X, sT))) return rc;
+            }
+            bt_ready = true;
+            GF2_CUDA_TRY(cudaEventRecord(b_ready, sT));
+        } else {
+            GF2_CUDA_TRY(cudaMemcpy2DAsync(dB.data, dB.stride_words * 8, B->data, B->stride_words * 8,
+                                           words_of(n) * 8, l, cudaMemcpyHostToDevice, sB));
+            if (b_ready) GF2_CUDA_TRY(cudaEventRecord(b_ready, sB));
+        }
     }
     if (hC && m && n) {
         dC.data = reinterpret_cast<uint64_t *>(base + offC);
@@ -1010,7 +1044,7 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
                                            words_of(n) * 8, m, cudaMemcpyHostToDevice, s));
     }
     if (!tuning) {
-        rc = mul_device(&dC, &dA, &dB, plans[0], o.accumulate, base, s, b_ready);
+        rc = mul_device(&dC, &dA, &dB, plans[0], o.accumulate, base, s, b_ready, bt_ready);
         if (rc) return rc;
     } else {
         // time every candidate on these operands (each computes the same C)

@@ -604,6 +604,11 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                             C32[w32] = P.accumulate ? (C32[w32] ^ v) : v;
                         }
                     }
+                    // the high half of the row's last 64-bit word can lie past
+                    // the last tile (no tile holds a column there): written as
+                    // zero like every bit past the last column
+                    const int64_t wn = (int64_t)(tn + 1) * G;
+                    if (half == 1 && !P.accumulate && wn < 2 * nW && 32 * wn >= T.n) C32[wn] = 0u;
                 }
             }
         }

@@ -293,13 +293,18 @@ def test_host_operands_through_the_abi():
     assert_same_bits(C, oracle.mul_packed(A, B, m, l, n), n, "host operands")
 
 
-@pytest.mark.parametrize("base,depth", [(g.GF2_BASE_M4RM, 2), (g.GF2_BASE_M4RM, 3), (g.GF2_BASE_TC_FP8, 2),
-                                        (g.GF2_BASE_M4RM, 0)])
-def test_host_operands_with_b_copied_beside_a_additions(base, depth):
+@pytest.mark.parametrize("base,depth,l", [(g.GF2_BASE_M4RM, 2, 1500), (g.GF2_BASE_M4RM, 3, 1500),
+                                          (g.GF2_BASE_TC_FP8, 2, 1500), (g.GF2_BASE_M4RM, 0, 1500),
+                                          (g.GF2_BASE_TC_FP4, 0, 1500), (g.GF2_BASE_TC_FP4, 1, 1500),
+                                          (g.GF2_BASE_TC_FP4, 2, 5000), (g.GF2_BASE_TC_S8, 1, 1500)])
+def test_host_operands_with_b_copied_beside_a_additions(base, depth, l):
     """Both factors on the host: B's copy runs on a side stream while A's
-    Strassen-Winograd additions run; every call, back to back, with new
-    contents each time (a stale B would show)."""
-    m, l, n = 1300, 1500, 1100
+    Strassen-Winograd additions (and, for the expanded tensor-core base
+    cases, A's expansion) run; for the tensor-core base cases B arrives in
+    row blocks, each transposed as the next one is copied (ragged last
+    block); every call, back to back, with new contents each time (a stale B
+    would show)."""
+    m, n = 1300, 1100
     for trial in range(3):
         A, B = inputs(m, l, n, seeds=(60 + trial, 70 + trial))
         C = np.full((m, synth.padded_stride(n)), 0xFFFF, np.uint64)

@@ -144,8 +144,11 @@ def test_fp4_pair_tile_columns(n, accumulate):
     A = synth.random_packed(m, l, 41)
     B = synth.random_packed(l, n, 42)
     ref = oracle.mul_packed(A, B, m, l, n)
-    C0 = synth.random_packed(m, n, 43) if accumulate else None
     if accumulate:
+        C0 = synth.random_packed(m, n, 43)
         ref = ref ^ C0
+    else:
+        # garbage everywhere, tail bits included: the product must zero them
+        C0 = np.full((m, synth.padded_stride(n)), 0xFFFFFFFFFFFFFFFF, np.uint64)
     got = tc_mul(A, B, m, l, n, accumulate=accumulate, C0=C0, base=g.GF2_BASE_TC_FP4)
     assert_same_bits(got, ref, n, "fp4 pair n=%d acc=%d" % (n, accumulate))
