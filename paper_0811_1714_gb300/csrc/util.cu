@@ -160,7 +160,10 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
 // holds rows i + 32 k (k < 8) of the block, 4 words each, so every row's 32
 // bytes are read by one lane (whole sectors); each 64 x 64 sub-block is four
 // 32 x 32 shuffle transposes with its off-diagonal quarters swapped, and
-// lane i ends with 4 consecutive words of 8 rows of T, written whole.
+// lane i ends with 4 consecutive words of 8 rows of T, written whole.  V16:
+// rows of X and T start on 16-byte boundaries, so words move in pairs
+// (16-byte loads and stores: half the memory transactions).
+template <bool V16>
 __global__ void __launch_bounds__(256) transpose_kernel(DMat T, DMat X)
 {
     const int lane = threadIdx.x & 31;
@@ -177,10 +180,20 @@ __global__ void __launch_bounds__(256) transpose_kernel(DMat T, DMat X)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int64_t r = rb * 256 + 32 * k + lane;
+            const uint64_t *xr = X.p + r * X.ld;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < 4; c += 2) {
                 const int64_t w = cb * 4 + c;
-                x[k][c] = (r < X.rows && w < XW) ? (X.p[r * X.ld + w] & word_mask(w, X.cols)) : 0ull;
+                if (V16) {
+                    // words w and w + 1 (w even; w + 1 is still inside the even stride)
+                    ulonglong2 v = make_ulonglong2(0ull, 0ull);
+                    if (r < X.rows && w < XW) v = *reinterpret_cast<const ulonglong2 *>(xr + w);
+                    x[k][c] = v.x & word_mask(w, X.cols);
+                    x[k][c + 1] = v.y & word_mask(w + 1, X.cols);
+                } else {
+                    x[k][c] = (r < X.rows && w < XW) ? (xr[w] & word_mask(w, X.cols)) : 0ull;
+                    x[k][c + 1] = (r < X.rows && w + 1 < XW) ? (xr[w + 1] & word_mask(w + 1, X.cols)) : 0ull;
+                }
             }
         }
 #pragma unroll
@@ -202,10 +215,17 @@ __global__ void __launch_bounds__(256) transpose_kernel(DMat T, DMat X)
             for (int h = 0; h < 2; ++h) {
                 const int64_t t = (cb * 4 + c) * 64 + 32 * h + lane;
                 if (t >= T.rows) continue;
+                uint64_t *tr = T.p + t * T.ld;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < 4; q += 2) {
                     const int64_t w = rb * 4 + q;
-                    if (w < TW) T.p[t * T.ld + w] = o[h][q] & word_mask(w, T.cols);
+                    const uint64_t v0 = o[h][q] & word_mask(w, T.cols), v1 = o[h][q + 1] & word_mask(w + 1, T.cols);
+                    if (V16 && w + 1 < TW) {
+                        *reinterpret_cast<ulonglong2 *>(tr + w) = make_ulonglong2(v0, v1);
+                    } else {
+                        if (w < TW) tr[w] = v0;
+                        if (w + 1 < TW) tr[w + 1] = v1;
+                    }
                 }
             }
         }
@@ -329,8 +349,13 @@ int transpose_launch(DMat T, DMat X, cudaStream_t s)
     if (nblk <= 0) return GF2_OK;
     int64_t blocks = (nblk * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
+    const bool v16 = (X.ld % 2 == 0) && (T.ld % 2 == 0) && !(reinterpret_cast<uintptr_t>(X.p) & 15) &&
+                     !(reinterpret_cast<uintptr_t>(T.p) & 15);
     ProfScope ps(PF_TRANSPOSE, s);
-    transpose_kernel<<<(unsigned)blocks, 256, 0, s>>>(T, X);
+    if (v16)
+        transpose_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(T, X);
+    else
+        transpose_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(T, X);
     note_launch();
     return check_launch();
 }
