@@ -303,21 +303,28 @@ def roofline_for(fam, leaves, M, L, N, k, ms_per_launch, peaks, peak_kind):
             "peak_note": note}
 
 
-def strassen_stream_bytes(M, L, N, d):
+def strassen_stream_bytes(M, L, N, d, leaf_bytes_per_entry=0.125):
     """Algorithmic HBM bytes per product of the Strassen-Winograd additions
     (padded sizes M, L, N, depth d), following the launch schedule: splits
     go top-down two levels per launch (reading the parents of A, M x L, and
-    of B, L x N, writing 49 or 7 children each); combines go bottom-up two
-    levels per launch (reading 7^j products of level j, writing level j-2 or
-    j-1, C-sized at level 0)."""
+    of B, L x N, writing 49 or 7 children each; the last level's children at
+    `leaf_bytes_per_entry`: 1/8 packed, 1/2 or 1 when they are written
+    expanded for the FP4 or FP8 base case, by a single-level split of their
+    own); combines go bottom-up two levels
+    per launch (reading 7^j products of level j, writing level j-2 or j-1,
+    C-sized at level 0)."""
     split = comb = 0.0
+    fused = leaf_bytes_per_entry != 0.125
     j = 1
     while j <= d:
         step = 2 if d - j + 1 >= 2 else 1
+        if fused and step == 2 and j + 1 == d:
+            step = 1                      # the expanded leaves come from a single-level split
         jt = j + step - 1
         parents = 7 ** (j - 1)
         children = 7 ** jt
-        split += (parents * (M * L + L * N) / 4 ** (j - 1) + children * (M * L + L * N) / 4 ** jt) / 8.0
+        out = leaf_bytes_per_entry if jt == d else 0.125
+        split += parents * (M * L + L * N) / 4 ** (j - 1) / 8.0 + children * (M * L + L * N) / 4 ** jt * out
         j += step
     j = d
     while j >= 1:
@@ -422,8 +429,10 @@ def measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak
         if dom in BASE_FAMILIES else None
     hbm = {}
     Mp, Lp, Np = (int(x) for x in kv["padded"].split("x"))
-    sb, cb = strassen_stream_bytes(Mp, Lp, Np, d)
-    eb = expand_bytes(kv.get("base"), leaves, M, L, N)
+    fused = kv.get("fused_expand") == "1"
+    leaf_bpe = {"tc_fp4": 0.5, "tc_fp8": 1.0}.get(kv.get("base"), 0.125) if fused else 0.125
+    sb, cb = strassen_stream_bytes(Mp, Lp, Np, d, leaf_bpe)
+    eb = 0.0 if fused else expand_bytes(kv.get("base"), leaves, M, L, N)
     for fam_name, nbytes in (("sw_split", sb), ("sw_combine", cb), ("expand", eb)):
         if fam_name in fam and nbytes > 0:
             per_step_ms = fam[fam_name]["ms"] / steps

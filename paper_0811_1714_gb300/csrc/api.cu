@@ -280,6 +280,8 @@ int make_plan(int64_t m, int64_t l, int64_t n, const gf2_opts &o, Plan *p)
     return GF2_OK;
 }
 
+bool fuses_expansion(const Plan &p);
+
 std::string plan_text(const Plan &p)
 {
     char buf[512];
@@ -289,13 +291,26 @@ std::string plan_text(const Plan &p)
              (long long)p.N, (long long)[&] { long long c = 1; for (int j = 0; j < p.depth; ++j) c *= 7; return c; }(),
              (long long)(p.M >> p.depth), (long long)(p.L >> p.depth), (long long)(p.N >> p.depth), p.k, p.t,
              p.bytes);
-    return p.cubic ? std::string(buf) + " cubic=1" : std::string(buf);
+    std::string t(buf);
+    if (p.cubic) t += " cubic=1";
+    if (fuses_expansion(p)) t += " fused_expand=1";
+    return t;
+}
+
+// Whether the last level of Algorithm 4's additions writes the leaf operands
+// expanded (expanded tensor-core base case below at least one level, leaf rows
+// needing no padding to whole 128-byte K blocks).
+bool fuses_expansion(const Plan &p)
+{
+    return is_expanded(p.base) && p.depth >= 1 &&
+           p.rowbytes == (kind_of(p.base) == KIND_F8 ? (p.L >> p.depth) : (p.L >> p.depth) / 2);
 }
 
 // Base case over `batch` products with dense or user layouts.
 int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const uint64_t *B,
              int64_t ldb, int64_t bsB, uint64_t *C, int64_t ldc, int64_t bsC, int64_t m, int64_t l,
-             int64_t n, int batch, int accumulate, char *scratch, cudaStream_t s, bool a_expanded = false)
+             int64_t n, int batch, int accumulate, char *scratch, cudaStream_t s, bool a_expanded = false,
+             bool b_expanded = false)
 {
     if (is_expanded(p.base)) {
         // expand the packed leaves once (HBM-bound), then the MMA kernel
@@ -304,7 +319,7 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
         uint8_t *XA = reinterpret_cast<uint8_t *>(scratch + p.offXA);
         uint8_t *XB = reinterpret_cast<uint8_t *>(scratch + p.offXB);
         int rc = a_expanded ? GF2_OK : tc_expand_launch(kind, A, lda, bsA, m, l, batch, XA, p.rowbytes, s);
-        if (!rc) rc = tc_expand_launch(kind, B, ldb, bsB, n, l, batch, XB, p.rowbytes, s);
+        if (!rc && !b_expanded) rc = tc_expand_launch(kind, B, ldb, bsB, n, l, batch, XB, p.rowbytes, s);
         if (rc) return rc;
         TcxLaunch X;
         X.kind = kind;
@@ -347,6 +362,10 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     const uint64_t *Bsrc = B->data;
     int64_t ldBsrc = B->stride_words;
     const int d = p.depth;
+    // expanded tensor-core base cases: the last level of additions writes the
+    // leaf operands already expanded (no packed leaves, no expansion pass)
+    // when the leaves' rows need no padding to whole 128-byte K blocks
+    const bool fused = fuses_expansion(p);
     // the left factor's additions need nothing of B: with B still arriving
     // (b_ready), they run first and B's work waits for the event
     auto split_A = [&](int j, int step, int64_t cnt) {
@@ -364,12 +383,24 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         }
         SA.out = reinterpret_cast<uint64_t *>(scratch + p.offA[jt]);
         SA.cld = p.ldA[jt]; SA.cbs = p.slabA[jt];
+        if (fused && jt == d) {
+            SA.xout = reinterpret_cast<uint8_t *>(scratch + p.offXA);
+            SA.rowbytes = p.rowbytes;
+            SA.xkind = kind_of(p.base) + 1;
+        }
         return step == 2 ? sw_split2_launch(SA, s) : sw_split_launch(SA, s);
+    };
+    // the fused expansion writes the leaves from a single-level split (the
+    // two-level one, holding 28 operand blocks per thread, writes 49 expanded
+    // leaves at half the HBM rate)
+    auto split_step = [&](int j) {
+        const int st = (d - j + 1 >= 2) ? 2 : 1;
+        return (fused && st == 2 && j + 1 == d) ? 1 : st;
     };
     if (d > 0) {
         int64_t cnt = 1;
         for (int j = 1; j <= d;) {
-            const int step = (d - j + 1 >= 2) ? 2 : 1;
+            const int step = split_step(j);
             int rc = split_A(j, step, cnt);
             if (rc) return rc;
             cnt *= (step == 2) ? 49 : 7;
@@ -378,8 +409,8 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     }
     // the expanded tensor-core base cases: A's leaves are expanded before B
     // is needed, so that this runs while B is still arriving
-    bool a_expanded = false;
-    if (is_expanded(p.base) && !(d == 0 && p.cubic)) {
+    bool a_expanded = fused;
+    if (!fused && is_expanded(p.base) && !(d == 0 && p.cubic)) {
         int64_t cntA = 1;
         for (int j = 0; j < d; ++j) cntA *= 7;
         const uint64_t *XA = d == 0 ? A->data : reinterpret_cast<const uint64_t *>(scratch + p.offA[d]);
@@ -424,7 +455,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     // never leave registers)
     int64_t cnt = 1;
     for (int j = 1; j <= d;) {
-        const int step = (d - j + 1 >= 2) ? 2 : 1;
+        const int step = split_step(j);
         const int jt = j + step - 1;                       // level written
         const int64_t Lp = p.L >> (j - 1), Np = p.N >> (j - 1);
         SplitLaunch SB;
@@ -451,6 +482,11 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         }
         SB.out = reinterpret_cast<uint64_t *>(scratch + p.offB[jt]);
         SB.cld = p.ldB[jt]; SB.cbs = p.slabB[jt];
+        if (fused && jt == d) {
+            SB.xout = reinterpret_cast<uint8_t *>(scratch + p.offXB);
+            SB.rowbytes = p.rowbytes;
+            SB.xkind = kind_of(p.base) + 1;
+        }
         const int rc = step == 2 ? sw_split2_launch(SB, s) : sw_split_launch(SB, s);
         if (rc) return rc;
         cnt *= (step == 2) ? 49 : 7;
@@ -462,7 +498,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         int rc = run_base(p, reinterpret_cast<const uint64_t *>(scratch + p.offA[d]), p.ldA[d], p.slabA[d],
                           reinterpret_cast<const uint64_t *>(scratch + p.offB[d]), p.ldB[d], p.slabB[d],
                           reinterpret_cast<uint64_t *>(scratch + p.offP[d]), p.ldP[d], p.slabP[d], Md, Ld,
-                          Nd, (int)cnt, 0, scratch, s, a_expanded);
+                          Nd, (int)cnt, 0, scratch, s, a_expanded, fused);
         if (rc) return rc;
     }
     // bottom-up: the 7 final additions of Algorithm 4, Augment and Stack,

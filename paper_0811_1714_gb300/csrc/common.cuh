@@ -89,6 +89,11 @@ struct SplitLaunch {
     const uint64_t *X; int64_t ld, bs; int64_t rows, cols, vrows, vcols;
     uint64_t *out; int64_t cld, cbs;
     int nparent; int side;
+    // xkind != 0: the children are written expanded for the tensor-core base
+    // case instead (KIND_F8 + 1 or KIND_F4 + 1): row r of child c at
+    // xout + (c * child rows + r) * rowbytes, rowbytes = the child's entries
+    // (FP8) or half of them (FP4), no padding
+    uint8_t *xout = nullptr; int64_t rowbytes = 0; int xkind = 0;
 };
 int sw_split_launch(const SplitLaunch &L, cudaStream_t s);
 

@@ -16,6 +16,7 @@
 // extent (vrows x vcols) read as zeros -- the virtual padding of Section 4 --
 // and the combine writes back only the real extent, tail bits cleared.
 #include "common.cuh"
+#include "expand.cuh"
 
 namespace gf2 {
 namespace {
@@ -42,6 +43,53 @@ __device__ __forceinline__ uint4 ld_virtual(const uint64_t *X, int64_t ld, int64
     if (w < vW) a = row[w] & word_mask(w, vcols);
     if (w + 1 < vW) b = row[w + 1] & word_mask(w + 1, vcols);
     return make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+}
+
+// One operand position (two words, row r of child c): packed (EX = 0) at
+// L.out, or expanded for the tensor-core base case (EX = KIND_F8 + 1 / KIND_F4
+// + 1): 128 or 64 bytes at L.xout, row (c * child rows + r), byte 64 w or 32 w.
+// COOP: the 32 lanes of the warp hold 64 consecutive words of one row (lane
+// i words w0 + 2i, w0 + 2i + 1), and the warp writes their expansion in
+// 512-byte rounds, 16 bytes per lane, fetching each chunk's source words by
+// shuffles (whole sectors per store instead of 16 bytes of every 64).
+template <int EX, bool COOP>
+__device__ __forceinline__ void st_child(const SplitLaunch &L, int64_t c, int64_t crows, int64_t r, int64_t w,
+                                         uint4 v)
+{
+    if (EX == 0) {
+        st4(L.out + c * L.cbs + r * L.cld + w, v);
+    } else if (!COOP) {
+        constexpr bool FP8 = EX == KIND_F8 + 1;
+        uint4 o[FP8 ? 8 : 4];
+        expand_words<FP8>(((uint64_t)v.y << 32) | v.x, ((uint64_t)v.w << 32) | v.z, o);
+        uint4 *d = reinterpret_cast<uint4 *>(L.xout + (c * crows + r) * L.rowbytes + w * (FP8 ? 64 : 32));
+#pragma unroll
+        for (int q = 0; q < (FP8 ? 8 : 4); ++q) d[q] = o[q];
+    } else {
+        constexpr bool FP8 = EX == KIND_F8 + 1;
+        constexpr int CPL = FP8 ? 8 : 4;                  // 16-byte chunks per lane's two words
+        const int lane = threadIdx.x & 31;
+        uint4 *d = reinterpret_cast<uint4 *>(L.xout + (c * crows + r) * L.rowbytes + (w - 2 * lane) * (FP8 ? 64 : 32));
+        // the 32-bit component a lane's chunks come from: FP4 component lane % 4
+        // (32 entries), FP8 component (lane % 8) / 2, 16-bit half lane % 2
+        const int comp = FP8 ? (lane & 7) >> 1 : lane & 3;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+            const int src = (32 * q + lane) / CPL;
+            const uint32_t a = __shfl_sync(0xffffffffu, v.x, src), b = __shfl_sync(0xffffffffu, v.y, src),
+                           e = __shfl_sync(0xffffffffu, v.z, src), f = __shfl_sync(0xffffffffu, v.w, src);
+            const uint32_t h = comp == 0 ? a : comp == 1 ? b : comp == 2 ? e : f;
+            uint4 o;
+            if (FP8) {
+                const uint32_t x = (lane & 1) ? (h >> 16) : h;
+                o = make_uint4(f8_of_nibble(x & 15u), f8_of_nibble((x >> 4) & 15u), f8_of_nibble((x >> 8) & 15u),
+                               f8_of_nibble((x >> 12) & 15u));
+            } else {
+                o = make_uint4(f4_of_byte(h), f4_of_byte(h >> 8), f4_of_byte(h >> 16), f4_of_byte(h >> 24));
+            }
+            d[32 * q + lane] = o;
+        }
+    }
 }
 
 // The 8 additions of Algorithm 4 for one position of the four quadrants:
@@ -85,7 +133,7 @@ __device__ __forceinline__ void combine_one(const uint4 (&p)[7], uint4 (&q)[4])
     q[0] = u0; q[1] = u4; q[2] = u5; q[3] = u6;
 }
 
-template <bool TOP>
+template <bool TOP, int EX, bool COOP>
 __global__ void __launch_bounds__(256) sw_split_kernel(SplitLaunch L)
 {
     const int64_t hr = L.rows / 2;            // child rows
@@ -114,9 +162,8 @@ __global__ void __launch_bounds__(256) sw_split_kernel(SplitLaunch L)
         }
         uint4 o[7];
         split_one(L.side, nw, ne, sw, se, o);
-        uint64_t *dst = L.out + (par * 7) * L.cbs + r * L.cld + w;
 #pragma unroll
-        for (int j = 0; j < 7; ++j) st4(dst + j * L.cbs, o[j]);
+        for (int j = 0; j < 7; ++j) st_child<EX, COOP>(L, par * 7 + j, hr, r, w, o[j]);
     }
 }
 
@@ -175,7 +222,7 @@ __global__ void __launch_bounds__(256) sw_combine_kernel(CombineLaunch L)
 // sub-blocks (q1 = quadrant, q2 = its quadrant) of one position of a parent
 // and writes the 49 operands of the grandchild products, product
 // 7 * (7 * parent + j1) + j2, the same order two single levels give.
-template <bool TOP>
+template <bool TOP, int EX, bool COOP>
 __global__ void __launch_bounds__(256) sw_split2_kernel(SplitLaunch L)
 {
     const int64_t qr = L.rows / 4;            // grandchild rows
@@ -206,13 +253,12 @@ __global__ void __launch_bounds__(256) sw_split2_kernel(SplitLaunch L)
 #pragma unroll
             for (int j = 0; j < 7; ++j) child[j][q2] = o[j];
         }
-        uint64_t *dst = L.out + (par * 49) * L.cbs + r * L.cld + w;
 #pragma unroll
         for (int j1 = 0; j1 < 7; ++j1) {
             uint4 g[7];
             split_one(L.side, child[j1][0], child[j1][1], child[j1][2], child[j1][3], g);
 #pragma unroll
-            for (int j2 = 0; j2 < 7; ++j2) st4(dst + (j1 * 7 + j2) * L.cbs, g[j2]);
+            for (int j2 = 0; j2 < 7; ++j2) st_child<EX, COOP>(L, par * 49 + j1 * 7 + j2, qr, r, w, g[j2]);
         }
     }
 }
@@ -295,11 +341,21 @@ int sw_split_launch(const SplitLaunch &L, cudaStream_t s)
     if (total <= 0) return GF2_OK;
     const bool top = (L.vrows != L.rows) || (L.vcols != L.cols) || (L.ld & 1) ||
                      (reinterpret_cast<uintptr_t>(L.X) & 15);
+    if (L.xkind && (!L.xout || (reinterpret_cast<uintptr_t>(L.xout) & 15) || (L.rowbytes & 15))) return GF2_ELAYOUT;
     ProfScope ps(PF_SPLIT, s);
-    if (top)
-        sw_split_kernel<true><<<grid_for(total), 256, 0, s>>>(L);
-    else
-        sw_split_kernel<false><<<grid_for(total), 256, 0, s>>>(L);
+    const unsigned g = (unsigned)grid_for(total);
+    // whole warps on one row's 64 words when a child row has a multiple of 32 word pairs
+    const bool coop = (L.cols / 256) % 32 == 0;
+    if (L.xkind == KIND_F8 + 1) {
+        if (coop) { if (top) sw_split_kernel<true, KIND_F8 + 1, true><<<g, 256, 0, s>>>(L); else sw_split_kernel<false, KIND_F8 + 1, true><<<g, 256, 0, s>>>(L); }
+        else { if (top) sw_split_kernel<true, KIND_F8 + 1, false><<<g, 256, 0, s>>>(L); else sw_split_kernel<false, KIND_F8 + 1, false><<<g, 256, 0, s>>>(L); }
+    } else if (L.xkind == KIND_F4 + 1) {
+        if (coop) { if (top) sw_split_kernel<true, KIND_F4 + 1, true><<<g, 256, 0, s>>>(L); else sw_split_kernel<false, KIND_F4 + 1, true><<<g, 256, 0, s>>>(L); }
+        else { if (top) sw_split_kernel<true, KIND_F4 + 1, false><<<g, 256, 0, s>>>(L); else sw_split_kernel<false, KIND_F4 + 1, false><<<g, 256, 0, s>>>(L); }
+    } else {
+        if (top) sw_split_kernel<true, 0, false><<<g, 256, 0, s>>>(L);
+        else sw_split_kernel<false, 0, false><<<g, 256, 0, s>>>(L);
+    }
     note_launch();
     return check_launch();
 }
@@ -310,11 +366,21 @@ int sw_split2_launch(const SplitLaunch &L, cudaStream_t s)
     if (total <= 0) return GF2_OK;
     const bool top = (L.vrows != L.rows) || (L.vcols != L.cols) || (L.ld & 1) ||
                      (reinterpret_cast<uintptr_t>(L.X) & 15);
+    if (L.xkind && (!L.xout || (reinterpret_cast<uintptr_t>(L.xout) & 15) || (L.rowbytes & 15))) return GF2_ELAYOUT;
     ProfScope ps(PF_SPLIT, s);
-    if (top)
-        sw_split2_kernel<true><<<grid_for(total), 256, 0, s>>>(L);
-    else
-        sw_split2_kernel<false><<<grid_for(total), 256, 0, s>>>(L);
+    const unsigned g = (unsigned)grid_for(total);
+    // whole warps on one row's 64 words when a child row has a multiple of 32 word pairs
+    const bool coop = (L.cols / 512) % 32 == 0;
+    if (L.xkind == KIND_F8 + 1) {
+        if (coop) { if (top) sw_split2_kernel<true, KIND_F8 + 1, true><<<g, 256, 0, s>>>(L); else sw_split2_kernel<false, KIND_F8 + 1, true><<<g, 256, 0, s>>>(L); }
+        else { if (top) sw_split2_kernel<true, KIND_F8 + 1, false><<<g, 256, 0, s>>>(L); else sw_split2_kernel<false, KIND_F8 + 1, false><<<g, 256, 0, s>>>(L); }
+    } else if (L.xkind == KIND_F4 + 1) {
+        if (coop) { if (top) sw_split2_kernel<true, KIND_F4 + 1, true><<<g, 256, 0, s>>>(L); else sw_split2_kernel<false, KIND_F4 + 1, true><<<g, 256, 0, s>>>(L); }
+        else { if (top) sw_split2_kernel<true, KIND_F4 + 1, false><<<g, 256, 0, s>>>(L); else sw_split2_kernel<false, KIND_F4 + 1, false><<<g, 256, 0, s>>>(L); }
+    } else {
+        if (top) sw_split2_kernel<true, 0, false><<<g, 256, 0, s>>>(L);
+        else sw_split2_kernel<false, 0, false><<<g, 256, 0, s>>>(L);
+    }
     note_launch();
     return check_launch();
 }

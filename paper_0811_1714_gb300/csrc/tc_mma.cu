@@ -54,6 +54,7 @@
 // copies and MMAs in flight, frees its tensor memory) instead of hanging.
 #include "common.cuh"
 #include "tcgen05.cuh"
+#include "expand.cuh"
 
 #include <algorithm>
 #include <cstdlib>
@@ -621,25 +622,6 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     if (PAIR) cluster_sync();
     fence_after();
     if (warp == MMA_WARP) free_tmem<PAIR>(tmem_base);
-}
-
-// 4 bits -> 4 bytes of 0x00 / 0x38 (E4M3 1.0): the multiply places bit i of
-// the nibble at bit 8i (the four shifted copies do not overlap), the mask
-// keeps those bits, the second multiply turns each into 0x38.
-__device__ __forceinline__ uint32_t f8_of_nibble(uint32_t v)
-{
-    return ((v * 0x00204081u) & 0x01010101u) * 0x38u;
-}
-
-// 8 bits -> 8 nibbles of 0x0 / 0x2 (E2M1 1.0), bit i in nibble i: spread by
-// halves, quarters and eighths, then shift each bit to nibble bit 1.
-__device__ __forceinline__ uint32_t f4_of_byte(uint32_t v)
-{
-    v &= 0xFFu;
-    v = (v | (v << 12)) & 0x000F000Fu;
-    v = (v | (v << 6)) & 0x03030303u;
-    v = (v | (v << 3)) & 0x11111111u;
-    return v << 1;
 }
 
 // Rows of a batch of packed matrices (rows x cols, stride ld, batch stride

@@ -150,3 +150,22 @@ def test_batched_table_bytes_follow_each_row_block_k():
     want = (1024 * 64 * 128 / 64 + 76 * 64 * 128 / 32 + 1024 * 64 * 128 / 64 + 276 * 64 * 128 / 32
             + 200 * 64 * 128 / 32)
     assert b == pytest.approx(want)
+
+
+def test_strassen_bytes_with_leaves_written_expanded():
+    """When the last level of additions writes the leaves expanded (FP4: half
+    a byte per entry instead of an eighth), only that level's writes grow,
+    by 4x; the parents read and the other levels stay packed."""
+    M = L = N = 32768
+    packed, comb = bench.strassen_stream_bytes(M, L, N, 2)
+    fused, comb2 = bench.strassen_stream_bytes(M, L, N, 2, 0.5)
+    leaves_packed = 49 * (M * L + L * N) / 16 / 8.0
+    level1 = 7 * (M * L + L * N) / 4 / 8.0
+    assert comb2 == comb
+    # depth 2 fused: level 1 is written and read back packed, then the
+    # leaves are written expanded (4x their packed bytes)
+    assert fused - packed == pytest.approx(2 * level1 + leaves_packed * 3)
+    # depth 3: levels 1-2 fused in one launch, level 3 alone writes the leaves
+    p3, _ = bench.strassen_stream_bytes(M, L, N, 3)
+    f3, _ = bench.strassen_stream_bytes(M, L, N, 3, 1.0)
+    assert f3 - p3 == pytest.approx(343 * (M * L + L * N) / 64 / 8.0 * 7)
