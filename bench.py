@@ -1041,6 +1041,18 @@ def run_peaks(args, rank, world, local_rank):
             "note": "CUDA-event time of the second of two identical launches per probe"}
 
 
+def emit(line):
+    """Print the JSON line as the last line of stdout: output that native
+    libraries buffered in C stdio (NCCL prints its version there) is
+    flushed first, so it cannot follow the line at exit."""
+    try:
+        import ctypes
+        ctypes.CDLL(None).fflush(None)
+    except (OSError, AttributeError):
+        pass
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1048,7 +1060,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args)), flush=True)
+            emit(run_reference(args))
         return
     if world > 1:
         import torch
@@ -1061,24 +1073,27 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % int(os.environ.get("MASTER_PORT", "29533")),
                                 rank=0, world_size=1)
+    def finish(line):
+        # the process group (and whatever its library prints on the way out)
+        # is closed before rank 0 prints the one JSON line
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            dist.barrier()
+            dist.destroy_process_group()
+        if rank == 0:
+            emit(line)
+
     if args.workload in ("batched", "chain", "sweep", "sharded", "peaks"):
         run = {"batched": run_batched, "chain": run_chain, "sweep": run_sweep, "sharded": run_sharded,
                "peaks": run_peaks}[args.workload]
-        line = run(args, rank, world, local_rank)
-        if rank == 0:
-            print(json.dumps(line), flush=True)
+        finish(run(args, rank, world, local_rank))
         return
     line = run_ours(args, rank, world, local_rank)
     if world == 1 and not args.no_configs:
         line["configs"] = run_configs(args, rank, world, local_rank)
-    if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds)
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-        dist.destroy_process_group()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.n, args.cpu_seconds)
+    finish(line)
 
 
 if __name__ == "__main__":
