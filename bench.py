@@ -826,13 +826,13 @@ def run_batched(args, rank, world, local_rank):
             tc_rl = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
                      "traffic": None, "kernel_ms_per_launch": t_ms / t_n,
                      "peak_note": "%g x bf16 burst of %s peaks (nominal ratio)" % (ratio, peak_kind),
-                     "work_note": "2 m l n of the 4096 products over the time of the whole graph (batched "
-                                  "transpose, expansion and MMA kernel; tiles of 128 x 256 entries of C pad "
-                                  "small products)"}
+                     "work_note": "2 m l n of the 4096 products over the time of the whole graph "
+                                  "(expansion of A, transposed expansion of B, MMA kernel; tiles of "
+                                  "128 x 256 entries of C pad small products)"}
         tcs[tname] = {"ms_per_step": tc_ms, "value": tc_value, "gpu_launches": tc_launches, "roofline": tc_rl,
                       "clocks": clocks.get(tname),
-                      "graph": "batched transpose of every B + batched expansion + one persistent tensor-core "
-                               "kernel",
+                      "graph": "batched expansion of every A and transposed expansion of every B + one "
+                               "persistent tensor-core kernel",
                       "freivalds_sampled_products_failed": sampled_bad(9)}
     ops = ops_all
     return {
@@ -844,7 +844,7 @@ def run_batched(args, rank, world, local_rank):
                    "variant": g.gf2_batched_variant_name(variant), "total_bit_ops": ops},
         "gpu_launches": launches, "roofline": rl, "clocks": clocks.get("m4rm"),
         "l2": "operands of all products (about 0.5 GB) exceed the 129 MB L2",
-        "graph": "each step replays one CUDA graph: counter reset + one persistent kernel",
+        "graph": "each step replays one CUDA graph: counter reset + one persistent kernel (two for a split variant)",
         "verified": {"freivalds_sampled_products_failed": bad},
         "tensor_core_bases": tcs,
     }
