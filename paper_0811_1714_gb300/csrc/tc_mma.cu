@@ -79,13 +79,13 @@ constexpr int PTN_F4 = 224;                   // tile columns of the FP4 pairs (
 
 // Tensor-memory columns of a tile width: accumulator b at b * ACC, FP4 scale
 // factors (32 columns each, every byte 1.0) at SFA and SFB.  256-column tiles
-// hold one FP4 accumulator (scale factors at 256 and 320); 224- and
-// 192-column tiles two (at 0 and 256, scale factors in the columns after
-// each); 128-column tiles two (at 0 and 128).
+// hold one FP4 accumulator (scale factors at 256 and 320); 224-column tiles
+// two (at 0 and 256, scale factors in the 32 columns after each); 128-column
+// tiles two (at 0 and 128).
 template <int TN> struct Cols {
-    static constexpr uint32_t ACC = (TN == 224 || TN == 192) ? 256 : TN;
-    static constexpr uint32_t SFA = TN == 224 ? 224 : TN == 192 ? 192 : 256;
-    static constexpr uint32_t SFB = TN == 224 ? 480 : TN == 192 ? 448 : 320;
+    static constexpr uint32_t ACC = TN == 224 ? 256 : TN;
+    static constexpr uint32_t SFA = TN == 224 ? 224 : 256;
+    static constexpr uint32_t SFB = TN == 224 ? 480 : 320;
 };
 
 // Per-CTA stage and ring: KBS 128-byte K blocks per stage; per block one CTA
@@ -329,8 +329,8 @@ template <int KIND, int PAIR, int TN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Params P)
 {
-    static_assert(TN == 256 || ((TN == 224 || TN == 192) && PAIR) || (TN == 128 && !PAIR),
-                  "tile widths: 256, 224 or 192 on pairs, 128 on one CTA");
+    static_assert(TN == 256 || (TN == 224 && PAIR) || (TN == 128 && !PAIR),
+                  "tile widths: 256, 224 on pairs, 128 on one CTA");
     constexpr int KBS = PAIR ? KBS_PAIR : KBS_ONE;
     using R = Ring<PAIR, KBS, TN>;
     constexpr int NACC = Fmt<KIND>::nacc(TN);
@@ -592,10 +592,9 @@ tc_mma_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
                         }
                     }
                 } else {
-                    // 224- and 192-column tiles: the column halves end on
-                    // 32-bit boundaries, so 32-bit words of C (the low and high
-                    // halves of its little-endian 64-bit words), each owned by
-                    // one tile
+                    // 224-column tiles: the column halves end on 32-bit
+                    // boundaries, so 32-bit words of C (the low and high halves
+                    // of its little-endian 64-bit words), each owned by one tile
                     uint32_t *C32 = reinterpret_cast<uint32_t *>(C);
 #pragma unroll
                     for (int g = 0; g < GH; ++g) {
