@@ -38,15 +38,15 @@ NCU_TRAFFIC = {
     "m4rm": {"sha": "1e46ef05f46c7c8d", "sources": ["paper_0811_1714_gb300/csrc/m4rm.cu",
                                                   "paper_0811_1714_gb300/csrc/m4rm_dev.cuh"],
              "bytes_per_operand_byte": 0.8845},
-    # profiles/tc_mma_kernel_fp4_n8192_depth1.md: 128.3 MB per launch against 117.4 MB of
+    # profiles/tc_mma_kernel_fp4_n8192_depth1.md: 128.5 MB per launch against 117.4 MB of
     # expanded leaf operands + 14.7 MB of packed leaf products
-    "tc_fp4": {"sha": "7383ceee517781f8", "sources": ["paper_0811_1714_gb300/csrc/tc_mma.cu",
+    "tc_fp4": {"sha": "b9164bcf051a8560", "sources": ["paper_0811_1714_gb300/csrc/tc_mma.cu",
                                                     "paper_0811_1714_gb300/csrc/tcgen05.cuh"],
-               "bytes_per_operand_byte": 0.971},
-    # profiles/tc_mma_kernel_fp8_n8192_depth1.md: 249.7 MB against 234.9 + 14.7 MB
-    "tc_fp8": {"sha": "7383ceee517781f8", "sources": ["paper_0811_1714_gb300/csrc/tc_mma.cu",
+               "bytes_per_operand_byte": 0.973},
+    # profiles/tc_mma_kernel_fp8_n8192_depth1.md: 249.1 MB against 234.9 + 14.7 MB
+    "tc_fp8": {"sha": "b9164bcf051a8560", "sources": ["paper_0811_1714_gb300/csrc/tc_mma.cu",
                                                     "paper_0811_1714_gb300/csrc/tcgen05.cuh"],
-               "bytes_per_operand_byte": 1.000},
+               "bytes_per_operand_byte": 0.998},
 }
 
 
@@ -425,7 +425,10 @@ def measure_product(g, torch, MC, MA, MB, m, l, n, o, steps, warmup, peaks, peak
     k = int(kv.get("m4rm_k", 8))
     dom = max(fam.items(), key=lambda kvp: kvp[1]["ms"])[0] if fam else None
     dom_ms = fam[dom]["ms"] / max(fam[dom]["launches"], 1) if fam else 0.0
-    rl = roofline_for(dom, leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
+    # leaves per launch of the dominant kernel: all of them, or one group of
+    # them when the leaf products are pipelined with the last level's additions
+    dom_leaves = leaves * steps / fam[dom]["launches"] if fam and fam[dom]["launches"] else leaves
+    rl = roofline_for(dom, dom_leaves, M, L, N, k, dom_ms, peaks, peak_kind) \
         if dom in BASE_FAMILIES else None
     hbm = {}
     Mp, Lp, Np = (int(x) for x in kv["padded"].split("x"))
