@@ -63,13 +63,14 @@ struct Arena {
 std::mutex g_arena_mu;   // guards the map, not the arenas
 std::map<std::pair<int, uintptr_t>, std::shared_ptr<Arena>> g_arenas;
 
-// One non-blocking side stream per device (created on first use), for
-// copies that overlap work on the caller's stream; ordered by events.
+// Non-blocking side streams per device (0, 1, 2; created on first use), for
+// copies and transposes that overlap work on the caller's stream; ordered by
+// events.
 cudaStream_t side_stream(int dev, int which = 0)
 {
     static std::mutex mu;
-    static cudaStream_t st[64][2] = {};
-    if (dev < 0 || dev >= 64 || which < 0 || which > 1) return nullptr;
+    static cudaStream_t st[64][3] = {};
+    if (dev < 0 || dev >= 64 || which < 0 || which > 2) return nullptr;
     std::lock_guard<std::mutex> lk(mu);
     cudaStream_t &x = st[dev][which];
     if (!x && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
@@ -348,8 +349,12 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
 }
 
 // C = A B (or C ^= A B) for device matrices on the current device.
+// b_leaves: the right factor's leaves (and B^T) are already in the plan's
+// scratch from a call on the same B with the same plan apart from m (row
+// blocks of A), so B's transposition, additions and expansion are skipped.
 int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan &p, int accumulate,
-               char *scratch, cudaStream_t s, cudaEvent_t b_ready = nullptr, bool bt_ready = false)
+               char *scratch, cudaStream_t s, cudaEvent_t b_ready = nullptr, bool bt_ready = false,
+               bool b_leaves = false)
 {
     const int64_t m = p.m, l = p.l, n = p.n;
     if (m == 0 || n == 0) return GF2_OK;
@@ -426,7 +431,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     // the tensor-core base cases read B transposed
     if (tc) {
         uint64_t *Bt = reinterpret_cast<uint64_t *>(scratch + p.offBt);
-        if (!bt_ready) {
+        if (!bt_ready && !b_leaves) {
             DMat T{Bt, n, l, p.ldBt};
             DMat X{B->data, l, n, B->stride_words};
             int rc = transpose_launch(T, X, s);
@@ -447,7 +452,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     }
     if (d == 0)
         return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
-                        m, l, n, 1, accumulate, scratch, s, a_expanded);
+                        m, l, n, 1, accumulate, scratch, s, a_expanded, b_leaves && is_expanded(p.base));
 
     // top-down: the additions of Algorithm 4 (the left factor's above, the
     // right factor's here) for every sub-problem of each level; two levels
@@ -456,6 +461,11 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     int64_t cnt = 1;
     for (int j = 1; j <= d;) {
         const int step = split_step(j);
+        if (b_leaves) {
+            cnt *= (step == 2) ? 49 : 7;
+            j += step;
+            continue;
+        }
         const int jt = j + step - 1;                       // level written
         const int64_t Lp = p.L >> (j - 1), Np = p.N >> (j - 1);
         SplitLaunch SB;
@@ -498,7 +508,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         int rc = run_base(p, reinterpret_cast<const uint64_t *>(scratch + p.offA[d]), p.ldA[d], p.slabA[d],
                           reinterpret_cast<const uint64_t *>(scratch + p.offB[d]), p.ldB[d], p.slabB[d],
                           reinterpret_cast<uint64_t *>(scratch + p.offP[d]), p.ldP[d], p.slabP[d], Md, Ld,
-                          Nd, (int)cnt, 0, scratch, s, a_expanded, fused);
+                          Nd, (int)cnt, 0, scratch, s, a_expanded, fused || (b_leaves && is_expanded(p.base)));
         if (rc) return rc;
     }
     // bottom-up: the 7 final additions of Algorithm 4, Augment and Stack,
@@ -758,6 +768,152 @@ int mul_with_scratch(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_o
 
 namespace {
 
+// Row blocks of the host-buffer product: rows per block at least kHostBlockRows,
+// at most kHostBlocks blocks.  Measured at n = 32768 (FP4, depth 2) per call:
+// 1 block 8.80 ms, 2 blocks 8.52, 4 blocks 8.63 (the leaf products of thinner
+// blocks lose more on the MMA launches than the extra overlap hides).
+constexpr int64_t kHostBlockRows = 8192;
+constexpr int kHostBlocks = 2;
+
+int host_row_blocks(int64_t m, const Plan &p)
+{
+    if (p.cubic) return 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kHostBlocks, m / kHostBlockRows));
+}
+
+// C = A B with A, B and C in host memory, A and C in nblk row blocks: every
+// row of C depends only on the same row of A, so block i of C is the product
+// A_i B, and the right factor's transposition, additions and expansion (the
+// same for every block) are done once.  The copies run on side streams: A_0,
+// then B (in row blocks, each transposed on a second side stream for the
+// tensor-core base cases while the next crosses the link), then A_1, ...; the
+// product of block i waits for A_i, and C_i's copy back to the host (the
+// other direction of the link) runs while block i + 1 is computed.
+int mul_host_blocks(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts &oc, int nblk,
+                    cudaStream_t s, int dev)
+{
+    const int64_t m = A->rows, l = A->cols, n = B->cols;
+    const int64_t mb = round_up((m + nblk - 1) / nblk, 64);
+    Plan p;
+    int rc = make_plan(mb, l, n, oc, &p);
+    if (rc) return rc;
+    size_t total = (p.bytes + 255) & ~(size_t)255;
+    const size_t offA = total;
+    total += (staged_bytes(A) + 255) & ~(size_t)255;
+    const size_t offB = total;
+    total += (staged_bytes(B) + 255) & ~(size_t)255;
+    const size_t offC = total;
+    total += (staged_bytes(C) + 255) & ~(size_t)255;
+    void *scratch = nullptr;
+    ArenaHold hold;
+    if ((rc = arena_get(s, total, &scratch, &hold))) return rc;
+    char *base = static_cast<char *>(scratch);
+    cudaStream_t sIn = side_stream(dev, 0), sT = side_stream(dev, 1), sOut = side_stream(dev, 2);
+    if (!sIn || !sT || !sOut) return GF2_ECUDA;
+    struct Events {
+        std::vector<cudaEvent_t> e;
+        ~Events() { for (cudaEvent_t x : e) cudaEventDestroy(x); }
+        cudaEvent_t make()
+        {
+            cudaEvent_t x = nullptr;
+            if (cudaEventCreateWithFlags(&x, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+            e.push_back(x);
+            return x;
+        }
+    } ev;
+    gf2_mat dA = *A, dB = *B, dC = *C;
+    dA.data = reinterpret_cast<uint64_t *>(base + offA);
+    dA.stride_words = even_up(words_of(l));
+    dA.device = dev;
+    dB.data = reinterpret_cast<uint64_t *>(base + offB);
+    dB.stride_words = even_up(words_of(n));
+    dB.device = dev;
+    dC.data = reinterpret_cast<uint64_t *>(base + offC);
+    dC.stride_words = even_up(words_of(n));
+    dC.device = dev;
+    auto rows_of = [&](int i, int64_t *r0) {
+        *r0 = (int64_t)i * mb;
+        return std::max<int64_t>(0, std::min<int64_t>(m, *r0 + mb) - *r0);
+    };
+    // the input copies, in the order the products need them
+    cudaEvent_t start = ev.make();
+    if (!start) return GF2_ECUDA;
+    GF2_CUDA_TRY(cudaEventRecord(start, s));                // after the caller's earlier work
+    GF2_CUDA_TRY(cudaStreamWaitEvent(sIn, start, 0));
+    std::vector<cudaEvent_t> a_ready(nblk);
+    auto copy_A = [&](int i) {
+        int64_t r0 = 0;
+        const int64_t rows = rows_of(i, &r0);
+        if (rows)
+            GF2_CUDA_TRY(cudaMemcpy2DAsync(dA.data + r0 * dA.stride_words, dA.stride_words * 8,
+                                           A->data + r0 * A->stride_words, A->stride_words * 8,
+                                           words_of(l) * 8, rows, cudaMemcpyHostToDevice, sIn));
+        if (!(a_ready[i] = ev.make())) return GF2_ECUDA;
+        GF2_CUDA_TRY(cudaEventRecord(a_ready[i], sIn));
+        return GF2_OK;
+    };
+    if ((rc = copy_A(0))) return rc;
+    cudaEvent_t b_ready = ev.make();
+    if (!b_ready) return GF2_ECUDA;
+    const bool tr = is_tc(p.base);
+    if (tr) {
+        // row block [r0, r1) of B is columns [r0, r1) of B^T, words r0 / 64
+        // onwards of its rows
+        uint64_t *Bt = reinterpret_cast<uint64_t *>(base + p.offBt);
+        const int64_t ch = std::max<int64_t>(256, (l / 8 + 255) / 256 * 256);
+        for (int64_t r0 = 0; r0 < l; r0 += ch) {
+            const int64_t r1 = std::min(l, r0 + ch);
+            uint64_t *dst = dB.data + r0 * dB.stride_words;
+            GF2_CUDA_TRY(cudaMemcpy2DAsync(dst, dB.stride_words * 8, B->data + r0 * B->stride_words,
+                                           B->stride_words * 8, words_of(n) * 8, r1 - r0,
+                                           cudaMemcpyHostToDevice, sIn));
+            cudaEvent_t landed = ev.make();
+            if (!landed) return GF2_ECUDA;
+            GF2_CUDA_TRY(cudaEventRecord(landed, sIn));
+            GF2_CUDA_TRY(cudaStreamWaitEvent(sT, landed, 0));
+            DMat T{Bt + r0 / 64, n, r1 - r0, p.ldBt};
+            DMat X{dst, r1 - r0, n, dB.stride_words};
+            if ((rc = transpose_launch(T, X, sT))) return rc;
+        }
+        GF2_CUDA_TRY(cudaEventRecord(b_ready, sT));
+    } else {
+        GF2_CUDA_TRY(cudaMemcpy2DAsync(dB.data, dB.stride_words * 8, B->data, B->stride_words * 8,
+                                       words_of(n) * 8, l, cudaMemcpyHostToDevice, sIn));
+        GF2_CUDA_TRY(cudaEventRecord(b_ready, sIn));
+    }
+    for (int i = 1; i < nblk; ++i)
+        if ((rc = copy_A(i))) return rc;
+    // the products, each block's C copied back as soon as it is complete
+    for (int i = 0; i < nblk; ++i) {
+        int64_t r0 = 0;
+        const int64_t rows = rows_of(i, &r0);
+        if (!rows) break;
+        Plan pi = p;
+        pi.m = rows;
+        gf2_mat Ai = dA, Ci = dC;
+        Ai.data = dA.data + r0 * dA.stride_words;
+        Ai.rows = rows;
+        Ci.data = dC.data + r0 * dC.stride_words;
+        Ci.rows = rows;
+        GF2_CUDA_TRY(cudaStreamWaitEvent(s, a_ready[i], 0));
+        rc = mul_device(&Ci, &Ai, &dB, pi, 0, base, s, i == 0 ? b_ready : nullptr, i == 0 && tr, i > 0);
+        if (rc) return rc;
+        cudaEvent_t c_done = ev.make();
+        if (!c_done) return GF2_ECUDA;
+        GF2_CUDA_TRY(cudaEventRecord(c_done, s));
+        GF2_CUDA_TRY(cudaStreamWaitEvent(sOut, c_done, 0));
+        GF2_CUDA_TRY(cudaMemcpy2DAsync(C->data + r0 * C->stride_words, C->stride_words * 8, Ci.data,
+                                       Ci.stride_words * 8, words_of(n) * 8, rows, cudaMemcpyDeviceToHost,
+                                       sOut));
+    }
+    cudaEvent_t out_done = ev.make();
+    if (!out_done) return GF2_ECUDA;
+    GF2_CUDA_TRY(cudaEventRecord(out_done, sOut));
+    GF2_CUDA_TRY(cudaStreamWaitEvent(s, out_done, 0));
+    GF2_CUDA_TRY(cudaStreamSynchronize(s));
+    return GF2_OK;
+}
+
 }  // namespace
 
 // ====================================================================== C ABI
@@ -989,6 +1145,10 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
     }
 
     const bool hA = A->device == GF2_HOST, hB = B->device == GF2_HOST, hC = C->device == GF2_HOST;
+    if (hA && hB && hC && !tuning && !o.accumulate && m && l && n) {
+        const int nblk = host_row_blocks(m, plans[0]);
+        if (nblk > 1) return mul_host_blocks(C, A, B, cands[0], nblk, s, dev);
+    }
     size_t total = (most + 255) & ~(size_t)255;
     size_t offA = total, offB = 0, offC = 0;
     if (hA) { offA = total; total += (staged_bytes(A) + 255) & ~(size_t)255; }

@@ -312,6 +312,25 @@ def test_host_operands_with_b_copied_beside_a_additions(base, depth, l):
         assert_same_bits(C, oracle.mul_packed(A, B, m, l, n), n, "host operands %d %d %d" % (base, depth, trial))
 
 
+@pytest.mark.parametrize("base,depth,m,l", [(g.GF2_BASE_TC_FP4, 2, 40000, 5000), (g.GF2_BASE_TC_FP4, 1, 20000, 1500),
+                                            (g.GF2_BASE_TC_FP8, 2, 20000, 1500), (g.GF2_BASE_M4RM, 1, 40000, 1500),
+                                            (g.GF2_BASE_M4RM, 0, 17000, 1500), (g.GF2_BASE_TC_S8, 1, 16500, 1500),
+                                            (g.GF2_BASE_TC_FP4, 0, 16400, 700)])
+def test_host_operands_in_row_blocks(base, depth, m, l):
+    """A, B and C on the host with at least 2 x 8192 rows: A and C go in 2
+    row blocks (the last one ragged), block i's product starts once A_i has
+    arrived and C_i is copied back while the next block is computed, B's
+    transposition, additions and expansion done once for all blocks; two
+    calls back to back with new contents (a stale B or block would show)."""
+    n = 1100
+    for trial in range(2):
+        A, B = inputs(m, l, n, seeds=(80 + trial, 90 + trial))
+        C = np.full((m, synth.padded_stride(n)), 0xFFFF, np.uint64)
+        g.gf2_mul(g.mat(C, n), g.mat(A, l), g.mat(B, n), g.opts(base=base, depth=depth))
+        assert_same_bits(C, oracle.mul_packed(A, B, m, l, n), n,
+                         "host row blocks %d %d %d %d" % (base, depth, m, trial))
+
+
 def test_launch_count_grows():
     before = g.gf2_launch_count()
     gpu_mul(*inputs(64, 64, 64), 64, 64, 64, depth=0)
