@@ -352,9 +352,10 @@ int run_base(const Plan &p, const uint64_t *A, int64_t lda, int64_t bsA, const u
 // b_leaves: the right factor's leaves (and B^T) are already in the plan's
 // scratch from a call on the same B with the same plan apart from m (row
 // blocks of A), so B's transposition, additions and expansion are skipped.
+// b_only: only that preparation of B's leaves (A and C are not read).
 int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan &p, int accumulate,
                char *scratch, cudaStream_t s, cudaEvent_t b_ready = nullptr, bool bt_ready = false,
-               bool b_leaves = false)
+               bool b_leaves = false, bool b_only = false)
 {
     const int64_t m = p.m, l = p.l, n = p.n;
     if (m == 0 || n == 0) return GF2_OK;
@@ -402,7 +403,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         const int st = (d - j + 1 >= 2) ? 2 : 1;
         return (fused && st == 2 && j + 1 == d) ? 1 : st;
     };
-    if (d > 0) {
+    if (d > 0 && !b_only) {
         int64_t cnt = 1;
         for (int j = 1; j <= d;) {
             const int step = split_step(j);
@@ -415,7 +416,7 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
     // the expanded tensor-core base cases: A's leaves are expanded before B
     // is needed, so that this runs while B is still arriving
     bool a_expanded = fused;
-    if (!fused && is_expanded(p.base) && !(d == 0 && p.cubic)) {
+    if (!b_only && !fused && is_expanded(p.base) && !(d == 0 && p.cubic)) {
         int64_t cntA = 1;
         for (int j = 0; j < d; ++j) cntA *= 7;
         const uint64_t *XA = d == 0 ? A->data : reinterpret_cast<const uint64_t *>(scratch + p.offA[d]);
@@ -450,6 +451,11 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         return cubic_narrow_launch(A->data, A->stride_words, m, l, BT, p.ldBt, C->data, C->stride_words, n,
                                    accumulate, s);
     }
+    if (d == 0 && b_only)
+        return is_expanded(p.base) ? tc_expand_launch(kind_of(p.base), Bsrc, ldBsrc, 0, n, l, 1,
+                                                      reinterpret_cast<uint8_t *>(scratch + p.offXB),
+                                                      p.rowbytes, s)
+                                   : GF2_OK;
     if (d == 0)
         return run_base(p, A->data, A->stride_words, 0, Bsrc, ldBsrc, 0, C->data, C->stride_words, 0,
                         m, l, n, 1, accumulate, scratch, s, a_expanded, b_leaves && is_expanded(p.base));
@@ -501,6 +507,15 @@ int mul_device(const gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const Plan 
         if (rc) return rc;
         cnt *= (step == 2) ? 49 : 7;
         j += step;
+    }
+    if (b_only) {
+        // B's leaves expanded here when its last level of additions did not
+        const int64_t Ld = p.L >> d, Nd = p.N >> d;
+        return (is_expanded(p.base) && !fused)
+                   ? tc_expand_launch(kind_of(p.base), reinterpret_cast<const uint64_t *>(scratch + p.offB[d]),
+                                      p.ldB[d], p.slabB[d], Nd, Ld, (int)cnt,
+                                      reinterpret_cast<uint8_t *>(scratch + p.offXB), p.rowbytes, s)
+                   : GF2_OK;
     }
     // all 7^d leaf products in one launch of the base case
     {
@@ -784,11 +799,12 @@ int host_row_blocks(int64_t m, const Plan &p)
 // C = A B with A, B and C in host memory, A and C in nblk row blocks: every
 // row of C depends only on the same row of A, so block i of C is the product
 // A_i B, and the right factor's transposition, additions and expansion (the
-// same for every block) are done once.  The copies run on side streams: A_0,
-// then B (in row blocks, each transposed on a second side stream for the
-// tensor-core base cases while the next crosses the link), then A_1, ...; the
-// product of block i waits for A_i, and C_i's copy back to the host (the
-// other direction of the link) runs while block i + 1 is computed.
+// same for every block) are done once, first.  The copies run on side
+// streams: B (in row blocks, each transposed on a second side stream for the
+// tensor-core base cases while the next crosses the link), then A_0, A_1,
+// ...; B's additions run while A_0 crosses the link, the product of block i
+// waits for A_i, and C_i's copy back to the host (the other direction of the
+// link) runs while block i + 1 is computed.
 int mul_host_blocks(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts &oc, int nblk,
                     cudaStream_t s, int dev)
 {
@@ -852,7 +868,6 @@ int mul_host_blocks(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_op
         GF2_CUDA_TRY(cudaEventRecord(a_ready[i], sIn));
         return GF2_OK;
     };
-    if ((rc = copy_A(0))) return rc;
     cudaEvent_t b_ready = ev.make();
     if (!b_ready) return GF2_ECUDA;
     const bool tr = is_tc(p.base);
@@ -881,9 +896,11 @@ int mul_host_blocks(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_op
                                        words_of(n) * 8, l, cudaMemcpyHostToDevice, sIn));
         GF2_CUDA_TRY(cudaEventRecord(b_ready, sIn));
     }
-    for (int i = 1; i < nblk; ++i)
+    for (int i = 0; i < nblk; ++i)
         if ((rc = copy_A(i))) return rc;
-    // the products, each block's C copied back as soon as it is complete
+    // B's leaves, then the products, each block's C copied back as soon as
+    // it is complete
+    if ((rc = mul_device(&dC, &dA, &dB, p, 0, base, s, b_ready, tr, false, true))) return rc;
     for (int i = 0; i < nblk; ++i) {
         int64_t r0 = 0;
         const int64_t rows = rows_of(i, &r0);
@@ -896,7 +913,7 @@ int mul_host_blocks(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_op
         Ci.data = dC.data + r0 * dC.stride_words;
         Ci.rows = rows;
         GF2_CUDA_TRY(cudaStreamWaitEvent(s, a_ready[i], 0));
-        rc = mul_device(&Ci, &Ai, &dB, pi, 0, base, s, i == 0 ? b_ready : nullptr, i == 0 && tr, i > 0);
+        rc = mul_device(&Ci, &Ai, &dB, pi, 0, base, s, nullptr, false, true);
         if (rc) return rc;
         cudaEvent_t c_done = ev.make();
         if (!c_done) return GF2_ECUDA;
