@@ -160,9 +160,10 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
 // holds rows i + 32 k (k < 8) of the block, 4 words each, so every row's 32
 // bytes are read by one lane (whole sectors); each 64 x 64 sub-block is four
 // 32 x 32 shuffle transposes with its off-diagonal quarters swapped, and
-// lane i ends with 4 consecutive words of 8 rows of T, written whole.  V16:
-// rows of X and T start on 16-byte boundaries, so words move in pairs
-// (16-byte loads and stores: half the memory transactions).
+// lane i ends with 4 consecutive words of 8 rows of T.  V16: rows of X and T
+// start on 16-byte boundaries, so words move in pairs (16-byte loads and
+// stores), and lanes 2j, 2j + 1 trade halves so that each store instruction
+// writes 16 whole 32-byte sectors instead of 32 halves.
 template <bool V16>
 __global__ void __launch_bounds__(256) transpose_kernel(DMat T, DMat X)
 {
@@ -214,18 +215,39 @@ __global__ void __launch_bounds__(256) transpose_kernel(DMat T, DMat X)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int64_t t = (cb * 4 + c) * 64 + 32 * h + lane;
-                if (t >= T.rows) continue;
-                uint64_t *tr = T.p + t * T.ld;
+                uint64_t v[4];
 #pragma unroll
-                for (int q = 0; q < 4; q += 2) {
-                    const int64_t w = rb * 4 + q;
-                    const uint64_t v0 = o[h][q] & word_mask(w, T.cols), v1 = o[h][q + 1] & word_mask(w + 1, T.cols);
-                    if (V16 && w + 1 < TW) {
-                        *reinterpret_cast<ulonglong2 *>(tr + w) = make_ulonglong2(v0, v1);
-                    } else {
-                        if (w < TW) tr[w] = v0;
-                        if (w + 1 < TW) tr[w + 1] = v1;
+                for (int q = 0; q < 4; ++q) v[q] = o[h][q] & word_mask(rb * 4 + q, T.cols);
+                if (V16) {
+                    // lanes 2j and 2j + 1 (rows t and t + 1 of T) trade halves so that
+                    // each 16-byte store pairs with its neighbour lane's into one whole
+                    // 32-byte sector: first both halves of the even lane's row, then
+                    // both halves of the odd lane's
+                    const int odd = lane & 1;
+                    const uint64_t s0 = odd ? v[0] : v[2], s1 = odd ? v[1] : v[3];
+                    const uint64_t r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+                    const int64_t w = rb * 4 + 2 * odd;
+                    const int64_t row0 = t - odd;                        // the even lane's row
+                    const uint64_t a0 = odd ? r0 : v[0], a1 = odd ? r1 : v[1];   // row0, words w, w + 1
+                    const uint64_t b0 = odd ? v[2] : r0, b1 = odd ? v[3] : r1;   // row0 + 1
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int64_t row = row0 + k;
+                        if (row >= T.rows) continue;
+                        uint64_t *tr = T.p + row * T.ld;
+                        const uint64_t x0 = k ? b0 : a0, x1 = k ? b1 : a1;
+                        if (w + 1 < TW) {
+                            *reinterpret_cast<ulonglong2 *>(tr + w) = make_ulonglong2(x0, x1);
+                        } else if (w < TW) {
+                            tr[w] = x0;
+                        }
                     }
+                } else {
+                    if (t >= T.rows) continue;
+                    uint64_t *tr = T.p + t * T.ld;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (rb * 4 + q < TW) tr[rb * 4 + q] = v[q];
                 }
             }
         }
