@@ -137,7 +137,10 @@ int gf2_free(gf2_mat *M);
  * operands are valid: C is cleared (or left alone when accumulating).
  * Device operands must all be on the current device; host operands
  * (device == GF2_HOST) are copied in and C is copied back inside the call,
- * which then returns only after the stream has finished it.
+ * which then returns only after the stream has finished it.  With A, B and
+ * C all on the host, m >= 16384 and accumulate 0, A and C go in two row
+ * blocks (C_i = A_i B, B's Strassen-Winograd additions done once), so that
+ * copies in either direction overlap the products; the result is the same.
  * Autotuning: when opts->base is GF2_BASE_AUTO and/or opts->depth is -1,
  * accumulate is 0 and m*l*n >= 2^36, the plan comes from the autotuner: a
  * cached choice for this (architecture, shape, options), or, on the first

@@ -80,6 +80,30 @@ cudaStream_t side_stream(int dev, int which = 0)
     return x;
 }
 
+// On an early return from a call that queued copies on side streams, the
+// caller's stream waits for whatever they still have queued (copies into the
+// arena) and is synchronised, so that the next user of the arena cannot
+// overwrite buffers still being copied.  Disarmed once the call has waited
+// for everything itself.
+struct SideJoin {
+    cudaStream_t s;
+    cudaStream_t side[3];
+    bool armed = true;
+    ~SideJoin()
+    {
+        if (!armed) return;
+        for (cudaStream_t x : side) {
+            if (!x || x == s) continue;
+            cudaEvent_t e = nullptr;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) break;
+            if (cudaEventRecord(e, x) == cudaSuccess) cudaStreamWaitEvent(s, e, 0);
+            cudaEventDestroy(e);
+        }
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+    }
+};
+
 struct ArenaHold {
     std::shared_ptr<Arena> arena;
     std::unique_lock<std::mutex> lock;
@@ -837,6 +861,7 @@ int mul_host_blocks(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_op
             return x;
         }
     } ev;
+    SideJoin join{s, {sIn, sT, sOut}};
     gf2_mat dA = *A, dB = *B, dC = *C;
     dA.data = reinterpret_cast<uint64_t *>(base + offA);
     dA.stride_words = even_up(words_of(l));
@@ -928,6 +953,7 @@ int mul_host_blocks(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_op
     GF2_CUDA_TRY(cudaEventRecord(out_done, sOut));
     GF2_CUDA_TRY(cudaStreamWaitEvent(s, out_done, 0));
     GF2_CUDA_TRY(cudaStreamSynchronize(s));
+    join.armed = false;                  // everything queued has been waited for
     return GF2_OK;
 }
 
@@ -1197,6 +1223,8 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
         cudaEvent_t a, b;
         ~EventGuard() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
     } guard{b_ready, s_ready};
+    SideJoin join{s, {sB, side_stream(dev, 1), nullptr}};
+    join.armed = hA || hB || hC;
     if (hA && m && l) {
         dA.data = reinterpret_cast<uint64_t *>(base + offA);
         dA.stride_words = even_up(words_of(l));
@@ -1291,6 +1319,7 @@ int gf2_mul(gf2_mat *C, const gf2_mat *A, const gf2_mat *B, const gf2_opts *opts
                                        words_of(n) * 8, m, cudaMemcpyDeviceToHost, s));
     }
     if (hA || hB || hC) GF2_CUDA_TRY(cudaStreamSynchronize(s));
+    join.armed = false;
     return GF2_OK;
 }
 
