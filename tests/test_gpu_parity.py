@@ -331,6 +331,31 @@ def test_host_operands_in_row_blocks(base, depth, m, l):
                          "host row blocks %d %d %d %d" % (base, depth, m, trial))
 
 
+@pytest.mark.parametrize("where", ["hdd", "dhd", "ddh", "hhd", "hdh", "dhh", "hhh"])
+@pytest.mark.parametrize("m", [1300, 16500])
+@pytest.mark.parametrize("acc", [0, 1])
+def test_host_and_device_operands_mixed(where, m, acc):
+    """Every mix of host (h) and device (d) operands, in the order A, B, C,
+    with C overwritten or accumulated into (a host C is then copied in
+    first): all three on the host with m >= 16384 and no accumulation takes
+    the row-blocked path, the rest the single-product one."""
+    l, n = 1500, 700
+    A, B = inputs(m, l, n, seeds=(110 + m % 7, 120 + acc))
+    C0 = synth.random_packed(m, n, 130 + acc)
+    ref = oracle.mul_packed(A, B, m, l, n) ^ (C0 if acc else 0)
+    hA = where[0] == "h"
+    hB = where[1] == "h"
+    hC = where[2] == "h"
+    Ax = A if hA else to_dev(A)
+    Bx = B if hB else to_dev(B)
+    Cx = C0.copy() if hC else to_dev(C0)
+    g.gf2_mul(g.mat(Cx, n), g.mat(Ax, l), g.mat(Bx, n),
+              g.opts(base=g.GF2_BASE_TC_FP4, depth=1, accumulate=acc))
+    torch.cuda.synchronize()
+    got = Cx if hC else to_host(Cx)
+    assert_same_bits(got, ref, n, "mixed %s m=%d acc=%d" % (where, m, acc))
+
+
 def test_launch_count_grows():
     before = g.gf2_launch_count()
     gpu_mul(*inputs(64, 64, 64), 64, 64, 64, depth=0)
